@@ -1,0 +1,25 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA path through the C ABI)")
+    config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+@pytest.fixture(scope="session")
+def tiny_sp4():
+    import synth
+    return synth.diamond_system(2, "sp4", 6.0, 6.0)
+
+
+@pytest.fixture(scope="session")
+def tiny_spd13():
+    import synth
+    return synth.diamond_system(2, "spd13", 7.0, 7.0)
