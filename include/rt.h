@@ -1,0 +1,251 @@
+/*
+ * rt.h — C ABI of the GB300 (sm_103a) library for one time step of the
+ * spatially truncated density matrix in a non-orthogonal, atom-blocked basis
+ * (O'Rourke & Bowler, "Linear scaling density matrix real time TDDFT:
+ * propagator unitarity & matrix truncation", arXiv:1404.5776).
+ *
+ * The method (paper Sec. II.A-II.B, Sec. IV, Sec. V.A):
+ *   rho(r,r') = sum phi_ia(r) K_ia,jb phi_jb(r')            (density matrix K)
+ *   S_ab = <phi_a|phi_b>                                     (overlap)
+ *   i dK/dt = S^-1 H K - K H S^-1,  K(t) = U K(t0) U^dagger  (Liouville equation)
+ *   U_EM(t+dt,t) = exp(-i S^-1 H(t+dt/2) dt)                 (eq. EM, Taylor, 6 terms)
+ *   S^-1 by Hotelling's iteration X <- X(2I - S X) at t = 0  (Sec. V.A)
+ *   H(t) = H0 - E_j(t) D_j,  D_j = <phi|r_j|phi>             (Sec. II.B, dv = -E r)
+ *   charge Tr(K S), dipole Tr(K D_j)                          (Sec. IV, Sec. II.B)
+ *   every matrix cut to a spatial radius                      (Sec. II.A)
+ * An added propagator mode uses the Crank-Nicolson form
+ *   U = (S + i dt/2 H)^-1 (S - i dt/2 H)
+ * with the inverse by Hotelling's iteration warm-started from the previous step.
+ *
+ * Conventions of every entry point:
+ *   - Pointers named h_* or documented "host" are host memory; the library
+ *     copies from them before returning and keeps no reference.
+ *   - Atom positions, cell lengths and radii are in Angstrom; matrix values,
+ *     energies, time and field in atomic units.
+ *   - Block-CSR: rowptr[n_atoms+1], col[nnzb] ascending within each row, values
+ *     as consecutive row-major b_i x b_j blocks in row order (b_i = bsize[i]).
+ *     Complex values are interleaved (re, im) doubles.
+ *   - A block (i,j) of a pattern with radius r exists iff the minimum-image
+ *     distance of atoms i and j is strictly below r, evaluated in FP64 as
+ *       dx = x_j - x_i; dx -= L*rint(dx/L); d2 = (dx*dx + dy*dy) + dz*dz; d2 < r*r
+ *     with every operation separately rounded.
+ *   - All GPU work is enqueued on the stream given to rt_create.  Functions
+ *     that return data to the host synchronise that stream.
+ *   - Every call returns an rt_status; rt_last_error(ctx) gives the reason of the
+ *     last failure.  After RT_ECUDA, RT_ETIMEOUT or RT_EINTERNAL the context is
+ *     poisoned: every later call except rt_last_error/rt_destroy returns RT_ESTATE.
+ *   - Device memory comes from the allocator passed to rt_create (cudaMalloc
+ *     when it is NULL) and is owned by the context until rt_destroy.
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RT_API __attribute__((visibility("default")))
+#else
+#define RT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_ctx rt_ctx;
+
+typedef enum {
+  RT_OK = 0,
+  RT_EINVAL = 1,     /* invalid argument (message says which)             */
+  RT_ENOMEM = 2,     /* device allocation failed                         */
+  RT_ECUDA = 3,      /* CUDA runtime error (poisons the context)         */
+  RT_ENOTCONV = 4,   /* Hotelling iteration diverged or hit max_iter     */
+  RT_ENUMERIC = 5,   /* NaN/Inf in an observable                         */
+  RT_ETIMEOUT = 6,   /* a bounded device wait gave up (poisons)          */
+  RT_EINTERNAL = 7,  /* internal consistency check failed (poisons)      */
+  RT_ESTATE = 8      /* call not valid in the context's current state    */
+} rt_status;
+
+enum { RT_PROP_EM = 0, RT_PROP_CN = 1 };
+enum { RT_FP64 = 0, RT_FP32 = 1 };
+enum { RT_FIELD_NONE = 0, RT_FIELD_GAUSSIAN = 1, RT_FIELD_CONSTANT = 2 };
+
+/* matrices readable with rt_get_matrix */
+enum {
+  RT_MAT_S = 0, RT_MAT_H0 = 1, RT_MAT_DX = 2, RT_MAT_DY = 3, RT_MAT_DZ = 4,
+  RT_MAT_SINV = 5, /* Hotelling S^-1 on P_Sinv                             */
+  RT_MAT_T = 6,    /* last T = S^-1 H(t+dt/2) on P_T (EM)                  */
+  RT_MAT_U = 7,    /* last propagator on P_U                               */
+  RT_MAT_K = 8,    /* density matrix of (sys, kick) on P_K                 */
+  RT_MAT_X = 9     /* CN warm-start inverse (S + i dt/2 H)^-1 on P_U       */
+};
+/* patterns readable with rt_get_pattern */
+enum {
+  RT_PAT_S = 0, RT_PAT_H = 1, RT_PAT_SINV = 2, RT_PAT_T = 3, RT_PAT_U = 4,
+  RT_PAT_K = 5, RT_PAT_M = 6, RT_PAT_A = 7, RT_PAT_W = 8
+};
+/* observables per step, per (system, kick): RT_NOBS doubles */
+enum {
+  RT_OBS_T = 0,          /* time at the end of the step (a.u.)            */
+  RT_OBS_TRKS_RE = 1, RT_OBS_TRKS_IM = 2,
+  RT_OBS_TRKDX_RE = 3, RT_OBS_TRKDX_IM = 4,
+  RT_OBS_TRKDY_RE = 5, RT_OBS_TRKDY_IM = 6,
+  RT_OBS_TRKDZ_RE = 7, RT_OBS_TRKDZ_IM = 8,
+  RT_OBS_HERM = 9,       /* max |K_ii - K_ii^dagger| before symmetrising   */
+  RT_OBS_HOT_ITERS = 10, /* CN Hotelling iterations this step              */
+  RT_OBS_HOT_RESID = 11, /* ||I - A X||_F / sqrt(n) of the last iteration  */
+  RT_NOBS = 12
+};
+
+/* Device allocator hook: return `bytes` of device memory usable on `stream`, or
+ * NULL on failure.  The free hook gets the same pointer back. */
+typedef void* (*rt_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*rt_free_fn)(void* ptr, void* stream, void* user);
+
+/* One system (host arrays, copied by rt_create). */
+typedef struct {
+  int32_t n_atoms;
+  const double* pos;        /* [n_atoms*3] Angstrom, wrapped into [0, cell)      */
+  const double* cell;       /* [3] orthorhombic cell lengths, NULL = open system  */
+  const int32_t* bsize;     /* [n_atoms] functions per atom, 1..13               */
+  double r_S, r_H;          /* radii of the given S and H/D patterns             */
+  const int32_t* s_rowptr;  /* S on P_{r_S} (symmetric, values real)             */
+  const int32_t* s_col;
+  const double* s_val;
+  const int32_t* h_rowptr;  /* H0 and D_x,y,z on P_{r_H}                          */
+  const int32_t* h_col;
+  const double* h_val;
+  const double* d_val[3];
+} rt_system;
+
+typedef struct {
+  double r_Sinv, r_T, r_U, r_K, r_M; /* truncation radii (Angstrom)                 */
+  double dt;                /* time step (a.u.)                                   */
+  int32_t prop;             /* RT_PROP_EM (paper) or RT_PROP_CN                    */
+  int32_t taylor_terms;     /* EM: terms of the exponential series in total (6)  */
+  double hot_tol;           /* Hotelling tolerance on ||I - S X||_F / sqrt(n)     */
+  int32_t hot_maxit;        /* Hotelling iteration cap for rt_inverse             */
+  int32_t hot_step_iters;   /* CN: Hotelling iterations per step                  */
+  int32_t precision;        /* RT_FP64 or RT_FP32 (block products in FP32, K,
+                               reductions and the last CN iteration in FP64)     */
+  int32_t full_step;        /* 1: rebuild U for every step; 0: reuse U            */
+  int32_t n_kick;           /* density matrices per system sharing U (1..3)       */
+  int32_t kick_terms;       /* Taylor terms of the kick exponential               */
+  int32_t obs_capacity;     /* steps kept in the observables buffer               */
+  int32_t use_graph;        /* capture the step in a CUDA graph and replay it     */
+} rt_params;
+
+typedef struct {
+  int32_t kind;             /* RT_FIELD_*                                         */
+  int32_t dir;              /* polarisation axis 0,1,2                            */
+  double E0, t0, sigma, omega; /* E(t) = E0 exp(-(t-t0)^2/(2 sigma^2)) cos(omega(t-t0)) */
+} rt_field;
+
+/* Fills the defaults: radii 8 A, dt 0.05, EM, 6 Taylor terms, tol 1e-10,
+ * maxit 100, 2 CN iterations per step, FP64, full step, 1 kick, 12 kick terms,
+ * 4096 observable steps, graphs on. */
+RT_API rt_status rt_default_params(rt_params* p);
+
+/* Creates a context for n_sys systems: validates and copies the host inputs,
+ * builds every pattern (S, H, S^-1, T, U, K, M, A = P_{max(r_S,r_H)},
+ * W = P_{r_U+r_S}) on the device with cell lists, and the triple lists of every
+ * product of the step.  Paper: spatial cut-off of Sec. II.A; atoms are
+ * stationary, so patterns are built once (Sec. V.A).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * alloc/free/alloc_user: device allocator (NULL = cudaMalloc/cudaFree).
+ * Errors: RT_EINVAL (inputs), RT_ENOMEM, RT_ECUDA. */
+RT_API rt_status rt_create(rt_ctx** ctx, const rt_system* sys, int32_t n_sys, const rt_params* p,
+                    void* cuda_stream, rt_alloc_fn alloc, rt_free_fn free_fn, void* alloc_user);
+
+/* External field E(t) along dir (Sec. II.B: dv_ext = -E_j(t) r, so H(t) =
+ * H0 - E(t) D_j; a Gaussian profile as in Sec. IV.A).  Default: none. */
+RT_API rt_status rt_set_field(rt_ctx* ctx, const rt_field* f);
+
+/* S^-1 for every system by Hotelling's iteration X <- X(2I - S X) from
+ * X0 = I/||S||_inf, each product cut to r_Sinv (Sec. V.A).  Stops when the
+ * residual ||I - S X||_F/sqrt(n) < hot_tol, or when it shrinks by less than a
+ * factor 0.9 (truncation floor; returns RT_OK).  RT_ENOTCONV when it grows
+ * above 1 or hot_maxit is reached.  iters/residual: host outputs of the
+ * system `sys` (may be NULL).  Synchronises. */
+RT_API rt_status rt_inverse(rt_ctx* ctx, int32_t sys, int32_t* iters, double* residual);
+
+/* Sets K of (sys, kick) from host values on P_K (complex interleaved, true
+ * block sizes; rt_pattern_size/rt_get_pattern give P_K). Resets time to 0. */
+RT_API rt_status rt_set_density(rt_ctx* ctx, int32_t sys, int32_t kick, const double* h_k_re_im);
+
+/* Ground-state K0 = f(S^-1 H0) S^-1 with the Fermi function f of chemical
+ * potential mu and temperature kT, by a Chebyshev expansion of `order` on the
+ * spectral interval [e_lo, e_hi] (set-up step, not part of the paper's
+ * propagation; needs rt_inverse).  Products cut to r_K; result symmetrised.
+ * Written to every kick slot of system `sys`. */
+RT_API rt_status rt_ground_state(rt_ctx* ctx, int32_t sys, int32_t order, double mu, double kT,
+                          double e_lo, double e_hi);
+
+/* Delta kick: K <- V K V^dagger, V = exp(+i kappa S^-1 D_dir) (H = H0 -
+ * kappa delta(t) D_dir, Sec. II.B), Taylor series of kick_terms terms with
+ * powers cut to r_U. Needs rt_inverse. */
+RT_API rt_status rt_kick(rt_ctx* ctx, int32_t sys, int32_t kick, int32_t dir, double kappa);
+
+/* Builds U for [t, t+dt] for every system (eq. EM at the midpoint, or the CN
+ * form) and keeps it for steps with full_step = 0. */
+RT_API rt_status rt_propagator(rt_ctx* ctx, double t);
+
+/* n time steps K <- U K U^dagger for every (system, kick), each followed by the
+ * observables.  With full_step, U is rebuilt at each step's midpoint. */
+RT_API rt_status rt_step(rt_ctx* ctx, int32_t n);
+
+/* Copies the observables recorded since the previous call for (sys, kick) to
+ * host `out` [max_steps][RT_NOBS] in step order; *n_out = steps copied.
+ * RT_ENUMERIC if any copied value is NaN/Inf (data still copied). */
+RT_API rt_status rt_observables(rt_ctx* ctx, int32_t sys, int32_t kick, double* out, int32_t max_steps,
+                         int32_t* n_out);
+
+/* Number of blocks of pattern `which` (RT_PAT_*) of system `sys`. */
+RT_API rt_status rt_pattern_size(rt_ctx* ctx, int32_t sys, int32_t which, int64_t* nnzb);
+/* Copies the pattern to host rowptr[n_atoms+1], col[nnzb]. */
+RT_API rt_status rt_get_pattern(rt_ctx* ctx, int32_t sys, int32_t which, int32_t* rowptr, int32_t* col);
+/* Number of doubles rt_get_matrix writes for `which` (2 per matrix element). */
+RT_API rt_status rt_matrix_size(rt_ctx* ctx, int32_t sys, int32_t which, int64_t* n_doubles);
+/* Copies matrix `which` (RT_MAT_*) of (sys, kick) to host, complex interleaved,
+ * true block sizes, on its pattern. capacity = doubles available in vals. */
+RT_API rt_status rt_get_matrix(rt_ctx* ctx, int32_t sys, int32_t kick, int32_t which, double* vals,
+                        int64_t capacity);
+
+/* Unitarity of the last propagator of `sys` (paper Sec. IV, eq. s_unit):
+ * with metric_S = 1, E = cut_{P_U}(U^dagger cut_{P_W}(S U)) - S (the conserved
+ * form in a non-orthogonal basis); with 0, E = cut_{P_U}(U^dagger U) - I (the
+ * printed form).  Host outputs max|E| and mean|E| over the entries of P_U. */
+RT_API rt_status rt_unitarity(rt_ctx* ctx, int32_t sys, int32_t metric_S, double* maxabs, double* meanabs);
+
+/* Algorithmic work of one step summed over systems and kicks:
+ * flops = sum over products of triples * (8 b^3 complex, 2 b^3 real), counted
+ * with the true block sizes (padding excluded); bytes = block values read
+ * and written by those products once each. */
+RT_API rt_status rt_step_work(rt_ctx* ctx, double* flops, double* bytes);
+
+/* Per-kernel-class timing: enable=1 makes later rt_step calls launch without
+ * a graph and bracket each kernel with CUDA events on the context stream;
+ * rt_profile_read returns, per class c < *n_classes (<= max), the launch
+ * count, total milliseconds, and algorithmic flops and bytes, with a name. */
+RT_API rt_status rt_profile(rt_ctx* ctx, int32_t enable);
+RT_API rt_status rt_profile_read(rt_ctx* ctx, int32_t max, int32_t* n_classes, int64_t* launches,
+                          double* ms, double* flops, double* bytes, char* names /* [max][32] */);
+
+/* Checkpoint: every K, the CN warm start, time, step counter.  With buf NULL,
+ * *bytes receives the size.  rt_set_state restores it (and clears poisoning). */
+RT_API rt_status rt_get_state(rt_ctx* ctx, void* buf, size_t* bytes);
+RT_API rt_status rt_set_state(rt_ctx* ctx, const void* buf, size_t bytes);
+
+/* Waits for all work of the context's stream. */
+RT_API rt_status rt_synchronize(rt_ctx* ctx);
+
+/* Reason of the last failure (never NULL; "" after success). */
+RT_API const char* rt_last_error(rt_ctx* ctx);
+
+RT_API void rt_destroy(rt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_H */

@@ -1,0 +1,586 @@
+// Elementwise and reduction kernels of the step: field update (Sec. II.B),
+// identity/Taylor initialisation (eq. matrix_exp), the Crank-Nicolson operands,
+// the traces Tr(K S) and Tr(K D_j) (Sec. IV charge, Sec. II.B dipole), the
+// unitarity measure of eq. s_unit, and deterministic fixed-order reductions.
+#include <cmath>
+
+#include "rt_elementwise.cuh"
+
+namespace rt {
+
+// ---------------------------------------------------------------------------
+// per-step device state
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double field_at(const FieldParams& f, double t) {
+  if (f.kind == RT_FIELD_GAUSSIAN) {
+    double x = t - f.t0;
+    return f.E0 * exp(-(x * x) / (2.0 * f.sigma * f.sigma)) * cos(f.omega * x);
+  }
+  if (f.kind == RT_FIELD_CONSTANT) return f.E0;
+  return 0.0;
+}
+
+__global__ void k_begin_step(DevState* s, FieldParams f, double dt, int n_herm) {
+  s->E_mid = field_at(f, s->t + 0.5 * dt);
+  for (int i = 0; i < n_herm; ++i) s->herm_bits[i] = 0ull;
+}
+
+__global__ void k_end_step(DevState* s, double dt) {
+  s->t += dt;
+  s->step += 1;
+}
+
+void launch_begin_step(DevState* s, const FieldParams& f, double dt, int n_herm, cudaStream_t st) {
+  k_begin_step<<<1, 1, 0, st>>>(s, f, dt, n_herm);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+void launch_end_step(DevState* s, double dt, cudaStream_t st) {
+  k_end_step<<<1, 1, 0, st>>>(s, dt);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// H(t+dt/2) = H0 - E D_j
+// ---------------------------------------------------------------------------
+__global__ void k_field_axpy(const double* __restrict__ H0, const double* __restrict__ D, const DevState* s,
+                             double scale, double* __restrict__ Hm, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double E = s ? s->E_mid * scale : scale;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) Hm[i] = H0[i] - E * D[i];
+}
+
+void launch_field_axpy(const double* H0, const double* D, const DevState* s, double scale, double* Hm, int64_t n,
+                       cudaStream_t st) {
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_field_axpy<<<(unsigned)g, 256, 0, st>>>(H0, D, s, scale, Hm, n);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// U = I + c1 T  (T on P_T mapped into P_U; U complex)
+// ---------------------------------------------------------------------------
+template <typename CV, typename RV>
+__global__ void k_taylor_init(CV* __restrict__ U, int64_t nnzb_u, const int32_t* __restrict__ u_rowidx,
+                              const int32_t* __restrict__ u_col, const RV* __restrict__ T,
+                              const int32_t* __restrict__ u_to_t, int B, double c1, int c1_imag, int ident) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb_u * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    double re = (ident && u_rowidx[q] == u_col[q] && r == c) ? 1.0 : 0.0;
+    double im = 0.0;
+    int tq = u_to_t ? u_to_t[q] : (int)q;
+    if (tq >= 0) {
+      double tv = (double)T[(int64_t)tq * NE + e];
+      if (c1_imag) im += c1 * tv;
+      else re += c1 * tv;
+    }
+    CV v;
+    v.x = (decltype(v.x))re;
+    v.y = (decltype(v.y))im;
+    U[idx] = v;
+  }
+}
+
+void launch_taylor_init(void* U, bool fp32, int64_t nnzb_u, const int32_t* u_rowidx, const int32_t* u_col,
+                        const void* T, bool t_fp32, const int32_t* u_to_t, int B, double c1, int c1_imag, int ident,
+                        cudaStream_t st) {
+  int64_t n = nnzb_u * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  if (!fp32 && !t_fp32)
+    k_taylor_init<double2, double><<<(unsigned)g, 256, 0, st>>>((double2*)U, nnzb_u, u_rowidx, u_col,
+                                                                (const double*)T, u_to_t, B, c1, c1_imag, ident);
+  else if (fp32 && !t_fp32)
+    k_taylor_init<float2, double><<<(unsigned)g, 256, 0, st>>>((float2*)U, nnzb_u, u_rowidx, u_col,
+                                                               (const double*)T, u_to_t, B, c1, c1_imag, ident);
+  else if (fp32 && t_fp32)
+    k_taylor_init<float2, float><<<(unsigned)g, 256, 0, st>>>((float2*)U, nnzb_u, u_rowidx, u_col,
+                                                              (const float*)T, u_to_t, B, c1, c1_imag, ident);
+  else
+    throw Error{RT_EINTERNAL, "taylor init variant"};
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// identity * scale on a pattern (real or complex FP64)
+// ---------------------------------------------------------------------------
+__global__ void k_identity(double* __restrict__ X, int cplx, int64_t nnzb, const int32_t* __restrict__ rowidx,
+                           const int32_t* __restrict__ col, int B, double scale) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    double v = (rowidx[q] == col[q] && r == c) ? scale : 0.0;
+    if (cplx) {
+      X[2 * idx] = v;
+      X[2 * idx + 1] = 0.0;
+    } else {
+      X[idx] = v;
+    }
+  }
+}
+
+void launch_identity(double* X, bool cplx, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B,
+                     double scale, cudaStream_t st) {
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_identity<<<(unsigned)g, 256, 0, st>>>(X, cplx ? 1 : 0, nnzb, rowidx, col, B, scale);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// gather a matrix onto another pattern through a block map (cut / zero-extend)
+// mode 0: real -> real, 1: real -> complex, 2: complex -> complex
+// ---------------------------------------------------------------------------
+__global__ void k_restrict(const double* __restrict__ src, double* __restrict__ dst, const int32_t* __restrict__ map,
+                           int64_t nnzb_dst, int NE, int mode) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; idx < nnzb_dst * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int sq = map[q];
+    if (mode == 0) {
+      dst[idx] = sq >= 0 ? src[(int64_t)sq * NE + e] : 0.0;
+    } else if (mode == 1) {
+      dst[2 * idx] = sq >= 0 ? src[(int64_t)sq * NE + e] : 0.0;
+      dst[2 * idx + 1] = 0.0;
+    } else {
+      dst[2 * idx] = sq >= 0 ? src[2 * ((int64_t)sq * NE + e)] : 0.0;
+      dst[2 * idx + 1] = sq >= 0 ? src[2 * ((int64_t)sq * NE + e) + 1] : 0.0;
+    }
+  }
+}
+
+void launch_restrict(const double* src, double* dst, const int32_t* map, int64_t nnzb_dst, int B, int mode,
+                     cudaStream_t st) {
+  int64_t n = nnzb_dst * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_restrict<<<(unsigned)g, 256, 0, st>>>(src, dst, map, nnzb_dst, B * B, mode);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// CN operands on P_A: A = S + i c H, Bm = S - i c H  (S, H gathered by maps)
+// ---------------------------------------------------------------------------
+__global__ void k_cn_operands(const double* __restrict__ S, const int32_t* __restrict__ a_to_s,
+                              const double* __restrict__ H, const int32_t* __restrict__ a_to_h, double c,
+                              double2* __restrict__ A, double2* __restrict__ Bm, int64_t nnzb_a, int NE) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; idx < nnzb_a * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int sq = a_to_s[q], hq = a_to_h[q];
+    double s = sq >= 0 ? S[(int64_t)sq * NE + e] : 0.0;
+    double h = hq >= 0 ? H[(int64_t)hq * NE + e] : 0.0;
+    A[idx] = make_double2(s, c * h);
+    Bm[idx] = make_double2(s, -c * h);
+  }
+}
+
+void launch_cn_operands(const double* S, const int32_t* a_to_s, const double* H, const int32_t* a_to_h, double c,
+                        double2* A, double2* Bm, int64_t nnzb_a, int B, cudaStream_t st) {
+  int64_t n = nnzb_a * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_cn_operands<<<(unsigned)g, 256, 0, st>>>(S, a_to_s, H, a_to_h, c, A, Bm, nnzb_a, B * B);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// deterministic reductions
+// ---------------------------------------------------------------------------
+constexpr int RED_T = 256;
+constexpr int RED_MAXB = 1024;
+
+// sum of vals[0..n) in a fixed order: per-block strided partial sums, then one
+// block adds the partials in index order.
+__global__ void k_sum_partials(const double* __restrict__ v, int64_t n, double* __restrict__ part) {
+  __shared__ double s[RED_T];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * RED_T + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_T) acc += v[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = RED_T / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) s[threadIdx.x] += s[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_sum_final(const double* __restrict__ part, int nb, double scale_sqrt_div, double* out,
+                            double* out2) {
+  __shared__ double s[RED_T];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += RED_T) acc += part[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = RED_T / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) s[threadIdx.x] += s[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double r = s[0];
+    if (scale_sqrt_div > 0.0) r = sqrt(r) / scale_sqrt_div;
+    *out = r;
+    if (out2) *out2 = r;
+  }
+}
+
+int reduce_blocks(int64_t n) {
+  int64_t b = (n + RED_T - 1) / RED_T;
+  if (b < 1) b = 1;
+  if (b > RED_MAXB) b = RED_MAXB;
+  return (int)b;
+}
+
+void launch_sum(const double* v, int64_t n, double* part, double sqrt_div, double* out, double* out2, cudaStream_t st) {
+  int nb = reduce_blocks(n);
+  k_sum_partials<<<nb, RED_T, 0, st>>>(v, n, part);
+  k_sum_final<<<1, RED_T, 0, st>>>(part, nb, sqrt_div, out, out2);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// Tr(K X) terms: for each block (i,j) of P_K, sum_ab K_ij[a,b] X_ji[b,a] over
+// the true functions; X gathered through kx_map (block (j,i) of X, or -1).
+// Four traces at once: X in {S, Dx, Dy, Dz}; results complex.
+__global__ void k_traces(const double2* __restrict__ K, int64_t nnzb, const int32_t* __restrict__ rowidx,
+                         const int32_t* __restrict__ col, const int32_t* __restrict__ bsize, int B,
+                         const double* __restrict__ S, const int32_t* __restrict__ ks_map,
+                         const double* __restrict__ Dx, const double* __restrict__ Dy, const double* __restrict__ Dz,
+                         const int32_t* __restrict__ kd_map, double* __restrict__ part) {
+  __shared__ double s[8][RED_T];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int NE = B * B;
+  for (int64_t q = (int64_t)blockIdx.x * RED_T + threadIdx.x; q < nnzb; q += (int64_t)gridDim.x * RED_T) {
+    int i = rowidx[q], j = col[q];
+    int bi = bsize[i], bj = bsize[j];
+    int sq = ks_map[q], dq = kd_map[q];
+    const double2* k = K + q * NE;
+    for (int a = 0; a < bi; ++a)
+      for (int b = 0; b < bj; ++b) {
+        double2 kv = k[a * B + b];
+        int te = b * B + a;  // X_ji[b][a]
+        if (sq >= 0) {
+          double x = S[(int64_t)sq * NE + te];
+          acc[0] += kv.x * x;
+          acc[1] += kv.y * x;
+        }
+        if (dq >= 0) {
+          double x = Dx[(int64_t)dq * NE + te];
+          acc[2] += kv.x * x;
+          acc[3] += kv.y * x;
+          x = Dy[(int64_t)dq * NE + te];
+          acc[4] += kv.x * x;
+          acc[5] += kv.y * x;
+          x = Dz[(int64_t)dq * NE + te];
+          acc[6] += kv.x * x;
+          acc[7] += kv.y * x;
+        }
+      }
+  }
+  for (int c = 0; c < 8; ++c) s[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int off = RED_T / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off)
+      for (int c = 0; c < 8; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 8; ++c) part[blockIdx.x * 8 + c] = s[c][0];
+}
+
+// Sums the trace partials in fixed order and writes one observables record.
+__global__ void k_traces_final(const double* __restrict__ part, int nb, const DevState* st, int herm_slot,
+                               double* __restrict__ ring, int capacity, int n_slots, int slot_index) {
+  __shared__ double s[8][RED_T];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < nb; i += RED_T)
+    for (int c = 0; c < 8; ++c) acc[c] += part[i * 8 + c];
+  for (int c = 0; c < 8; ++c) s[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int off = RED_T / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off)
+      for (int c = 0; c < 8; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int64_t step = st->step - 1;  // runs after the step counter advanced
+    int64_t r = step % capacity;
+    double* rec = ring + (r * n_slots + slot_index) * RT_NOBS;
+    rec[RT_OBS_T] = st->t;
+    // Tr(KX) = sum K X^T: real part from K.re, imaginary from K.im (X real)
+    rec[RT_OBS_TRKS_RE] = s[0][0];
+    rec[RT_OBS_TRKS_IM] = s[1][0];
+    rec[RT_OBS_TRKDX_RE] = s[2][0];
+    rec[RT_OBS_TRKDX_IM] = s[3][0];
+    rec[RT_OBS_TRKDY_RE] = s[4][0];
+    rec[RT_OBS_TRKDY_IM] = s[5][0];
+    rec[RT_OBS_TRKDZ_RE] = s[6][0];
+    rec[RT_OBS_TRKDZ_IM] = s[7][0];
+    rec[RT_OBS_HERM] = __longlong_as_double((long long)st->herm_bits[herm_slot]);
+    rec[RT_OBS_HOT_ITERS] = st->hot_iters;
+    rec[RT_OBS_HOT_RESID] = st->hot_resid;
+  }
+}
+
+void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const int32_t* col, const int32_t* bsize,
+                   int B, const double* S, const int32_t* ks_map, const double* Dx, const double* Dy,
+                   const double* Dz, const int32_t* kd_map, double* part, const DevState* st, int herm_slot,
+                   double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s) {
+  int nb = reduce_blocks(nnzb);
+  k_traces<<<nb, RED_T, 0, s>>>(K, nnzb, rowidx, col, bsize, B, S, ks_map, Dx, Dy, Dz, kd_map, part);
+  k_traces_final<<<1, RED_T, 0, s>>>(part, nb, st, herm_slot, ring, capacity, n_slots, slot_index);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// unitarity: |E - Ref| over the true entries of P_U (max and sum)
+// Ref = S gathered on P_U (metric) or the identity.
+// ---------------------------------------------------------------------------
+__global__ void k_unit_dev(const double2* __restrict__ E, int64_t nnzb, const int32_t* __restrict__ rowidx,
+                           const int32_t* __restrict__ col, const int32_t* __restrict__ bsize, int B,
+                           const double* __restrict__ S, const int32_t* __restrict__ us_map,
+                           double* __restrict__ part_max, double* __restrict__ part_sum) {
+  __shared__ double smax[RED_T], ssum[RED_T];
+  double mx = 0.0, sm = 0.0;
+  const int NE = B * B;
+  for (int64_t q = (int64_t)blockIdx.x * RED_T + threadIdx.x; q < nnzb; q += (int64_t)gridDim.x * RED_T) {
+    int i = rowidx[q], j = col[q];
+    int bi = bsize[i], bj = bsize[j];
+    int sq = us_map ? us_map[q] : -1;
+    for (int a = 0; a < bi; ++a)
+      for (int b = 0; b < bj; ++b) {
+        double2 e = E[q * NE + a * B + b];
+        double ref;
+        if (us_map) ref = sq >= 0 ? S[(int64_t)sq * NE + a * B + b] : 0.0;
+        else ref = (i == j && a == b) ? 1.0 : 0.0;
+        double dr = e.x - ref, di = e.y;
+        double d = sqrt(dr * dr + di * di);
+        mx = fmax(mx, d);
+        sm += d;
+      }
+  }
+  smax[threadIdx.x] = mx;
+  ssum[threadIdx.x] = sm;
+  __syncthreads();
+  for (int off = RED_T / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + off]);
+      ssum[threadIdx.x] += ssum[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part_max[blockIdx.x] = smax[0];
+    part_sum[blockIdx.x] = ssum[0];
+  }
+}
+
+int launch_unitarity_dev(const double2* E, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
+                         const int32_t* bsize, int B, const double* S, const int32_t* us_map, double* part_max,
+                         double* part_sum, cudaStream_t st) {
+  int nb = reduce_blocks(nnzb);
+  k_unit_dev<<<nb, RED_T, 0, st>>>(E, nnzb, rowidx, col, bsize, B, S, us_map, part_max, part_sum);
+  RT_CUDA_CHECK(cudaGetLastError());
+  return nb;
+}
+
+// ---------------------------------------------------------------------------
+// max_i sum_j |S_ij| over true entries (Gershgorin bound of Hotelling's X0)
+// ---------------------------------------------------------------------------
+__global__ void k_row_abs_sums(const double* __restrict__ S, const int32_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ bsize, int B, int n_atoms,
+                               double* __restrict__ rows) {
+  int i = blockIdx.x;
+  if (i >= n_atoms) return;
+  int bi = bsize[i];
+  for (int a = threadIdx.x; a < bi; a += blockDim.x) {
+    double acc = 0.0;
+    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+      int j = col[q];
+      for (int b = 0; b < bsize[j]; ++b) acc += fabs(S[(int64_t)q * B * B + a * B + b]);
+    }
+    rows[(int64_t)i * B + a] = acc;
+  }
+}
+
+__global__ void k_max_final(const double* __restrict__ v, int64_t n, double* out) {
+  __shared__ double s[RED_T];
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += RED_T) m = fmax(m, v[i]);
+  s[threadIdx.x] = m;
+  __syncthreads();
+  for (int off = RED_T / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + off]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+void launch_inf_norm(const double* S, const int32_t* rowptr, const int32_t* col, const int32_t* bsize, int B,
+                     int n_atoms, double* rows_tmp, double* out, cudaStream_t st) {
+  RT_CUDA_CHECK(cudaMemsetAsync(rows_tmp, 0, sizeof(double) * (size_t)n_atoms * B, st));
+  k_row_abs_sums<<<n_atoms, 32, 0, st>>>(S, rowptr, col, bsize, B, n_atoms, rows_tmp);
+  k_max_final<<<1, RED_T, 0, st>>>(rows_tmp, (int64_t)n_atoms * B, out);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev step of the Fermi-operator expansion (real FP64, on P_K):
+//   xy = (TY - a Y)/w;  Ynew = first ? xy : 2 xy - Yprev;  K += c Ynew
+// ---------------------------------------------------------------------------
+__global__ void k_cheb_step(const double* __restrict__ TY, const double* __restrict__ Y, const double* __restrict__ Yp,
+                            double* __restrict__ Yn, double* __restrict__ Kacc, double a, double w, double c, int first,
+                            int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double xy = (TY[i] - a * Y[i]) / w;
+    double yn = first ? xy : 2.0 * xy - Yp[i];
+    Yn[i] = yn;
+    Kacc[i] = Kacc[i] + c * yn;
+  }
+}
+
+void launch_cheb_step(const double* TY, const double* Y, const double* Yp, double* Yn, double* Kacc, double a,
+                      double w, double c, int first, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_cheb_step<<<(unsigned)g, 256, 0, st>>>(TY, Y, Yp, Yn, Kacc, a, w, c, first, n);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+__global__ void k_scale(double* __restrict__ v, double c, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = c * v[i];
+}
+
+void launch_scale(double* v, double c, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_scale<<<(unsigned)g, 256, 0, st>>>(v, c, n);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// K0 <- (K0 + K0^T)/2 as complex (imaginary zero), padded entries zero
+__global__ void k_symmetrise_to_complex(const double* __restrict__ Kr, double2* __restrict__ K, int64_t nnzb,
+                                        const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col,
+                                        const int32_t* __restrict__ tmap, const int32_t* __restrict__ bsize, int B) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    int i = rowidx[q], j = col[q];
+    double v = 0.0;
+    if (r < bsize[i] && c < bsize[j]) v = 0.5 * (Kr[idx] + Kr[(int64_t)tmap[q] * NE + c * B + r]);
+    K[idx] = make_double2(v, 0.0);
+  }
+}
+
+void launch_symmetrise_to_complex(const double* Kr, double2* K, int64_t nnzb, const int32_t* rowidx,
+                                  const int32_t* col, const int32_t* tmap, const int32_t* bsize, int B,
+                                  cudaStream_t st) {
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_symmetrise_to_complex<<<(unsigned)g, 256, 0, st>>>(Kr, K, nnzb, rowidx, col, tmap, bsize, B);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// precision conversions and the delta-form operand W = K + M (FP32)
+// ---------------------------------------------------------------------------
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
+}
+
+void launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_d2f<<<(unsigned)g, 256, 0, st>>>(a, b, n);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// W[q] = (float)K[mk[q]] + M[q] on P_M (complex)
+__global__ void k_delta_w(const double2* __restrict__ K, const int32_t* __restrict__ m_to_k,
+                          const float2* __restrict__ Mf, float2* __restrict__ Wf, int64_t nnzb_m, int NE) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; idx < nnzb_m * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int kq = m_to_k ? m_to_k[q] : (int)q;
+    float2 m = Mf[idx];
+    if (kq >= 0) {
+      double2 k = K[(int64_t)kq * NE + e];
+      m.x = (float)((double)m.x + k.x);
+      m.y = (float)((double)m.y + k.y);
+    }
+    Wf[idx] = m;
+  }
+}
+
+void launch_delta_w(const double2* K, const int32_t* m_to_k, const float2* Mf, float2* Wf, int64_t nnzb_m, int B,
+                    cudaStream_t st) {
+  int64_t n = nnzb_m * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_delta_w<<<(unsigned)g, 256, 0, st>>>(K, m_to_k, Mf, Wf, nnzb_m, B * B);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+__global__ void k_set_hot(DevState* s, const double* resid, int iters) {
+  s->hot_resid = *resid;
+  s->hot_iters = iters;
+}
+
+void launch_set_hot(DevState* s, const double* resid, int iters, cudaStream_t st) {
+  k_set_hot<<<1, 1, 0, st>>>(s, resid, iters);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// dU = U - I in FP32 (CN delta form)
+__global__ void k_u_minus_i_f32(const double2* __restrict__ U, float2* __restrict__ dU, int64_t nnzb,
+                                const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    double2 u = U[idx];
+    double d = (rowidx[q] == col[q] && r == c) ? 1.0 : 0.0;
+    dU[idx] = make_float2((float)(u.x - d), (float)u.y);
+  }
+}
+
+void launch_u_minus_i_f32(const double2* U, float2* dU, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
+                          int B, cudaStream_t st) {
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_u_minus_i_f32<<<(unsigned)g, 256, 0, st>>>(U, dU, nnzb, rowidx, col, B);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace rt

@@ -1,0 +1,1397 @@
+// C ABI and step orchestration of the GB300 density-matrix RT-TDDFT library.
+//
+// One time step (paper Sec. II.A, eq. EM, eq. matrix_exp, Sec. V.A):
+//   EM:  H(t+dt/2) = H0 - E D_j;  T = cut_{r_T}(S^-1 H);  T^n = cut_{r_U}(T T^{n-1});
+//        U = sum_{n<6} (-i dt)^n T^n / n!
+//   CN:  A = S + i dt/2 H, X <- X(2I - A X) (warm start), U = cut_{r_U}(X (S - i dt/2 H))
+//   M = cut_{r_M}(U K);  K' = M U^dagger on the upper blocks of P_K, mirrored;
+//   Tr(K S), Tr(K D_xyz) recorded per step.
+// All work runs on an internal stream ordered against the caller's stream with
+// events; a step is captured once in a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <tuple>
+
+#include "rt_elementwise.cuh"
+#include "rt_internal.cuh"
+
+namespace rt {
+
+// true multiply-adds of a triple list (block sizes without padding)
+int64_t triple_true_macs(const Triples& T, const Pattern& A, bool a_dag, const Pattern& C, const int32_t* bsize,
+                         Arena& arena, cudaStream_t st);
+
+enum ProfClass { PC_FIELD = 0, PC_T, PC_TAYLOR, PC_UK, PC_MUDAG, PC_CN_HOT, PC_CN_U, PC_OBS, PC_MISC, PC_N };
+static const char* kProfNames[PC_N] = {"field_update", "gemm_T=SinvH",  "gemm_taylor_powers",
+                                       "gemm_M=UK",    "gemm_K=MUdag",  "gemm_cn_hotelling",
+                                       "gemm_cn_U=XB", "traces",        "misc"};
+
+struct TripleKey {
+  const Pattern *A, *B, *C;
+  bool ad, bd, up;
+  bool operator<(const TripleKey& o) const {
+    return std::tie(A, B, C, ad, bd, up) < std::tie(o.A, o.B, o.C, o.ad, o.bd, o.up);
+  }
+};
+
+struct TripleInfo {
+  Triples t;
+  int64_t true_macs = 0;
+  int64_t nnzb_a = 0, nnzb_b = 0;
+  int64_t true_elems_a = 0, true_elems_b = 0, true_elems_c = 0;
+};
+
+struct Sys {
+  int n_atoms = 0, B = 0;
+  int64_t n_true = 0;
+  std::vector<int32_t> bsize;
+  int32_t* d_bsize = nullptr;
+  double* d_pos = nullptr;
+  bool periodic = false;
+  double cell[3] = {0, 0, 0};
+  double r_S = 0, r_H = 0;
+  std::vector<double> h_pos;
+  // patterns (owned by the context cache; several names may share one)
+  Pattern *pS = nullptr, *pH = nullptr, *pSinv = nullptr, *pT = nullptr, *pU = nullptr, *pK = nullptr,
+          *pM = nullptr, *pA = nullptr, *pW = nullptr;
+  std::map<double, std::unique_ptr<Pattern>> pcache;
+  std::unique_ptr<Pattern> pS_given, pH_given;
+  std::map<TripleKey, std::unique_ptr<TripleInfo>> tcache;
+  // FP64 values (padded blocks)
+  double *S = nullptr, *H0 = nullptr, *D[3] = {nullptr, nullptr, nullptr}, *Hm = nullptr;
+  double *Sinv = nullptr, *Zs = nullptr, *Xs2 = nullptr;
+  double *T = nullptr, *P0 = nullptr, *P1 = nullptr, *T0 = nullptr, *TD = nullptr;
+  double2 *U = nullptr, *M = nullptr;
+  std::vector<double2*> K;
+  double2 *Acn = nullptr, *Bcn = nullptr, *X = nullptr, *Xn = nullptr, *Zc = nullptr;
+  double2 *Sc = nullptr, *W = nullptr, *E = nullptr;
+  // FP32 buffers (mixed precision)
+  float *Tf = nullptr, *Pf0 = nullptr, *Pf1 = nullptr;
+  float2 *dUf = nullptr, *Kf = nullptr, *Mf = nullptr, *Wf = nullptr;
+  // maps
+  int32_t *u_to_t = nullptr, *a_to_s = nullptr, *a_to_h = nullptr, *k_to_sT = nullptr, *k_to_hT = nullptr;
+  int32_t *u_to_sinv = nullptr, *k_to_sinv = nullptr, *u_to_s = nullptr, *k_to_m = nullptr, *m_to_k = nullptr;
+  // reductions
+  double* red_items = nullptr;
+  int64_t red_items_n = 0;
+  double* red_part = nullptr;
+  double* scal = nullptr;  // device scalars [16]
+  double* rows_tmp = nullptr;
+  bool sinv_ready = false;
+  bool u_ready = false;
+  int sinv_iters = 0;
+  double sinv_resid = 0.0;
+  std::string sinv_status;
+};
+
+}  // namespace rt
+
+struct rt_ctx {
+  rt_params p{};
+  rt::Allocator alloc;
+  rt::Arena arena;
+  cudaStream_t user = nullptr;
+  cudaStream_t ws = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<std::unique_ptr<rt::Sys>> sys;
+  rt::FieldParams field;
+  rt::DevState* dstate = nullptr;
+  double* ring = nullptr;  // [capacity][n_slots][RT_NOBS]
+  int n_slots = 0;
+  int64_t host_step = 0;  // steps enqueued since the last time reset
+  std::vector<int64_t> read_upto;  // per slot: steps already returned
+  double t_host = 0.0;
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_dirty = true;
+  // profiling / counting
+  bool profiling = false;
+  bool counting = false;
+  double count_flops = 0.0, count_bytes = 0.0;
+  struct Prof {
+    int64_t launches = 0;
+    double ms = 0, flops = 0, bytes = 0;
+  } prof[rt::PC_N];
+  struct PendingEv {
+    cudaEvent_t a, b;
+    int cls;
+    double flops, bytes;
+  };
+  std::vector<PendingEv> pending;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+  bool poisoned = false;
+  std::string err;
+};
+
+namespace rt {
+
+// ----------------------------------------------------------------------------
+// helpers
+// ----------------------------------------------------------------------------
+template <class F>
+static void run(rt_ctx* c, int cls, double flops, double bytes, F&& f) {
+  if (c->counting) {
+    c->count_flops += flops;
+    c->count_bytes += bytes;
+    return;
+  }
+  if (c->profiling) {
+    std::pair<cudaEvent_t, cudaEvent_t> ev;
+    if (!c->ev_free.empty()) {
+      ev = c->ev_free.back();
+      c->ev_free.pop_back();
+    } else {
+      RT_CUDA_CHECK(cudaEventCreate(&ev.first));
+      RT_CUDA_CHECK(cudaEventCreate(&ev.second));
+    }
+    RT_CUDA_CHECK(cudaEventRecord(ev.first, c->ws));
+    f();
+    RT_CUDA_CHECK(cudaEventRecord(ev.second, c->ws));
+    c->pending.push_back({ev.first, ev.second, cls, flops, bytes});
+  } else {
+    f();
+  }
+}
+
+static void collect_profile(rt_ctx* c) {
+  if (c->pending.empty()) return;
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+  for (auto& pe : c->pending) {
+    float ms = 0.f;
+    RT_CUDA_CHECK(cudaEventElapsedTime(&ms, pe.a, pe.b));
+    auto& pr = c->prof[pe.cls];
+    pr.launches += 1;
+    pr.ms += ms;
+    pr.flops += pe.flops;
+    pr.bytes += pe.bytes;
+    c->ev_free.push_back({pe.a, pe.b});
+  }
+  c->pending.clear();
+}
+
+static Pattern* pattern_for(rt_ctx* c, Sys& s, double r) {
+  auto it = s.pcache.find(r);
+  if (it != s.pcache.end()) return it->second.get();
+  auto P = std::make_unique<Pattern>();
+  build_pattern(*P, s.n_atoms, s.d_pos, s.periodic ? s.cell : nullptr, r, c->arena, c->ws);
+  Pattern* raw = P.get();
+  s.pcache[r] = std::move(P);
+  return raw;
+}
+
+static TripleInfo& triples_for(rt_ctx* c, Sys& s, Pattern* A, bool ad, Pattern* B, bool bd, Pattern* C, bool up) {
+  TripleKey key{A, B, C, ad, bd, up};
+  auto it = s.tcache.find(key);
+  if (it != s.tcache.end()) return *it->second;
+  auto ti = std::make_unique<TripleInfo>();
+  build_triples(ti->t, *A, ad, *B, bd, *C, up, c->arena, c->ws);
+  ti->true_macs = triple_true_macs(ti->t, *A, ad, *C, s.d_bsize, c->arena, c->ws);
+  ti->nnzb_a = A->nnzb;
+  ti->nnzb_b = B->nnzb;
+  auto elems = [&](const Pattern* P) {
+    int64_t n = 0;
+    for (int i = 0; i < s.n_atoms; ++i)
+      for (int q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) n += (int64_t)s.bsize[i] * s.bsize[P->h_col[q]];
+    return n;
+  };
+  ti->true_elems_a = elems(A);
+  ti->true_elems_b = elems(B);
+  {
+    std::vector<int32_t> items(ti->t.n_items);
+    if (ti->t.n_items)
+      RT_CUDA_CHECK(cudaMemcpyAsync(items.data(), ti->t.item_blk, sizeof(int32_t) * ti->t.n_items,
+                                    cudaMemcpyDeviceToHost, c->ws));
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    std::vector<int32_t> rowof(C->nnzb);
+    for (int i = 0; i < s.n_atoms; ++i)
+      for (int q = C->h_rowptr[i]; q < C->h_rowptr[i + 1]; ++q) rowof[q] = i;
+    int64_t n = 0;
+    for (int32_t q : items) n += (int64_t)s.bsize[rowof[q]] * s.bsize[C->h_col[q]];
+    ti->true_elems_c = n;
+  }
+  if (ti->t.n_items > s.red_items_n) {
+    s.red_items = c->arena.get_n<double>(ti->t.n_items);
+    s.red_items_n = ti->t.n_items;
+  }
+  TripleInfo& ref = *ti;
+  s.tcache[key] = std::move(ti);
+  return ref;
+}
+
+static size_t nvals(const Sys& s, const Pattern* P) { return (size_t)P->nnzb * s.B * s.B; }
+
+static int32_t* block_map(rt_ctx* c, const Pattern* src, const Pattern* dst, bool transpose) {
+  int32_t* m = c->arena.get_n<int32_t>(src->nnzb);
+  if (transpose) build_transpose_map(m, *src, *dst, c->ws);
+  else build_block_map(m, *src, *dst, c->ws);
+  return m;
+}
+
+// algorithmic flops / bytes of a product (true block sizes): every block of
+// A and B read once, every output block written once
+static double gemm_flops(const TripleInfo& ti, bool cplx) { return (cplx ? 8.0 : 2.0) * (double)ti.true_macs; }
+static double gemm_bytes(const Sys&, const TripleInfo& ti, bool cplx, bool fp32) {
+  double bpe = (cplx ? 2.0 : 1.0) * (fp32 ? 4.0 : 8.0);
+  return bpe * (double)(ti.true_elems_a + ti.true_elems_b + ti.true_elems_c);
+}
+
+static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cplx, bool ad, bool bd, Epilogue epi,
+                 GemmArgs g, const Pattern* C) {
+  g.item_blk = ti.t.item_blk;
+  g.ptr = ti.t.ptr;
+  g.ab = ti.t.ab;
+  g.n_items = ti.t.n_items;
+  g.tri = &ti.t;
+  if (C) {
+    g.rowidx = C->rowidx;
+    g.colidx = C->col;
+    g.tmap = C->tmap;
+  }
+  g.bsize = s.d_bsize;
+  int B = s.B;
+  run(c, cls, gemm_flops(ti, cplx), gemm_bytes(s, ti, cplx, fp32),
+      [&] { launch_gemm(B, fp32, cplx, ad, bd, epi, g, c->ws); });
+}
+
+static GemmArgs args(const void* A, const void* B, void* C) {
+  GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  return g;
+}
+
+// residual ||I - Y||_F / sqrt(n) from the per-item partials of an EPI_TWO_I product
+static void residual_from_items(rt_ctx* c, Sys& s, const TripleInfo& ti, double* out, double* out2) {
+  run(c, PC_MISC, 0, 0, [&] {
+    launch_sum(s.red_items, ti.t.n_items, s.red_part, std::sqrt((double)s.n_true), out, out2, c->ws);
+  });
+}
+
+// ----------------------------------------------------------------------------
+// set-up
+// ----------------------------------------------------------------------------
+static void upload_padded(rt_ctx* c, Sys& s, const Pattern& P, const double* h_val, double* d_val,
+                          bool identity_pad) {
+  const int B = s.B;
+  std::vector<double> buf((size_t)P.nnzb * B * B, 0.0);
+  size_t o = 0;
+  for (int i = 0; i < s.n_atoms; ++i) {
+    for (int q = P.h_rowptr[i]; q < P.h_rowptr[i + 1]; ++q) {
+      int j = P.h_col[q];
+      int bi = s.bsize[i], bj = s.bsize[j];
+      double* blk = buf.data() + (size_t)q * B * B;
+      for (int a = 0; a < bi; ++a)
+        for (int b = 0; b < bj; ++b) blk[a * B + b] = h_val[o + (size_t)a * bj + b];
+      if (identity_pad && i == j)
+        for (int a = bi; a < B; ++a) blk[a * B + a] = 1.0;
+      o += (size_t)bi * bj;
+    }
+  }
+  RT_CUDA_CHECK(cudaMemcpyAsync(d_val, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->ws));
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+}
+
+static int pad_size(int bmax) {
+  if (bmax <= 1) return 1;
+  if (bmax <= 4) return 4;
+  if (bmax <= 13) return 13;
+  return -1;
+}
+
+static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
+  const rt_params& p = c->p;
+  RT_REQUIRE(in.n_atoms > 0, RT_EINVAL, "n_atoms must be positive");
+  RT_REQUIRE(in.pos && in.bsize && in.s_rowptr && in.s_col && in.s_val && in.h_rowptr && in.h_col && in.h_val,
+             RT_EINVAL, "NULL input array");
+  RT_REQUIRE(in.d_val[0] && in.d_val[1] && in.d_val[2], RT_EINVAL, "NULL dipole array");
+  s.n_atoms = in.n_atoms;
+  s.bsize.assign(in.bsize, in.bsize + in.n_atoms);
+  int bmax = 0;
+  s.n_true = 0;
+  for (int b : s.bsize) {
+    RT_REQUIRE(b >= 1 && b <= 13, RT_EINVAL, "bsize must be in 1..13");
+    bmax = std::max(bmax, b);
+    s.n_true += b;
+  }
+  s.B = pad_size(bmax);
+  s.periodic = in.cell != nullptr;
+  if (s.periodic) {
+    for (int d = 0; d < 3; ++d) {
+      s.cell[d] = in.cell[d];
+      RT_REQUIRE(s.cell[d] > 0, RT_EINVAL, "cell lengths must be positive");
+    }
+  }
+  s.r_S = in.r_S;
+  s.r_H = in.r_H;
+  RT_REQUIRE(s.r_S > 0 && s.r_H > 0, RT_EINVAL, "r_S and r_H must be positive");
+  s.h_pos.assign(in.pos, in.pos + 3 * (size_t)in.n_atoms);
+  for (int i = 0; i < s.n_atoms; ++i)
+    for (int d = 0; d < 3; ++d) {
+      double x = s.h_pos[3 * i + d];
+      RT_REQUIRE(std::isfinite(x), RT_EINVAL, "non-finite position");
+      if (s.periodic) RT_REQUIRE(x >= 0.0 && x < s.cell[d], RT_EINVAL, "positions must be wrapped into [0, cell)");
+    }
+  s.d_pos = c->arena.get_n<double>(3 * (size_t)s.n_atoms);
+  s.d_bsize = c->arena.get_n<int32_t>(s.n_atoms);
+  RT_CUDA_CHECK(cudaMemcpyAsync(s.d_pos, s.h_pos.data(), sizeof(double) * 3 * s.n_atoms, cudaMemcpyHostToDevice, c->ws));
+  RT_CUDA_CHECK(cudaMemcpyAsync(s.d_bsize, s.bsize.data(), sizeof(int32_t) * s.n_atoms, cudaMemcpyHostToDevice, c->ws));
+
+  // given patterns
+  s.pS_given = std::make_unique<Pattern>();
+  s.pH_given = std::make_unique<Pattern>();
+  upload_pattern(*s.pS_given, s.n_atoms, in.s_rowptr, in.s_col, s.r_S, c->arena, c->ws);
+  upload_pattern(*s.pH_given, s.n_atoms, in.h_rowptr, in.h_col, s.r_H, c->arena, c->ws);
+  s.pS = s.pS_given.get();
+  s.pH = s.pH_given.get();
+  // built patterns
+  s.pSinv = pattern_for(c, s, p.r_Sinv);
+  s.pT = pattern_for(c, s, p.r_T);
+  s.pU = pattern_for(c, s, p.r_U);
+  s.pK = pattern_for(c, s, p.r_K);
+  s.pM = pattern_for(c, s, p.r_M);
+  s.pA = pattern_for(c, s, std::max(s.r_S, s.r_H));
+
+  // values
+  s.S = c->arena.get_n<double>(nvals(s, s.pS));
+  s.H0 = c->arena.get_n<double>(nvals(s, s.pH));
+  s.Hm = c->arena.get_n<double>(nvals(s, s.pH));
+  upload_padded(c, s, *s.pS, in.s_val, s.S, true);
+  upload_padded(c, s, *s.pH, in.h_val, s.H0, false);
+  for (int d = 0; d < 3; ++d) {
+    s.D[d] = c->arena.get_n<double>(nvals(s, s.pH));
+    upload_padded(c, s, *s.pH, in.d_val[d], s.D[d], false);
+  }
+  // matrices of the step
+  s.Sinv = c->arena.get_n<double>(nvals(s, s.pSinv));
+  s.Zs = c->arena.get_n<double>(nvals(s, s.pSinv));
+  s.Xs2 = c->arena.get_n<double>(nvals(s, s.pSinv));
+  s.T = c->arena.get_n<double>(nvals(s, s.pT));
+  s.P0 = c->arena.get_n<double>(nvals(s, s.pU));
+  s.P1 = c->arena.get_n<double>(nvals(s, s.pU));
+  s.U = c->arena.get_n<double2>(nvals(s, s.pU));
+  s.M = c->arena.get_n<double2>(nvals(s, s.pM));
+  for (int k = 0; k < p.n_kick; ++k) {
+    double2* Kk = c->arena.get_n<double2>(nvals(s, s.pK));
+    RT_CUDA_CHECK(cudaMemsetAsync(Kk, 0, sizeof(double2) * nvals(s, s.pK), c->ws));
+    s.K.push_back(Kk);
+  }
+  s.red_part = c->arena.get_n<double>(1024 * 8);
+  s.scal = c->arena.get_n<double>(16);
+  s.rows_tmp = c->arena.get_n<double>((size_t)s.n_atoms * s.B);
+
+  // maps
+  if (s.pU != s.pT) s.u_to_t = block_map(c, s.pU, s.pT, false);
+  s.k_to_sT = block_map(c, s.pK, s.pS, true);
+  s.k_to_hT = block_map(c, s.pK, s.pH, true);
+  s.u_to_sinv = block_map(c, s.pU, s.pSinv, false);
+  s.k_to_sinv = block_map(c, s.pK, s.pSinv, false);
+  if (s.pK != s.pM) {
+    s.k_to_m = block_map(c, s.pK, s.pM, false);
+    s.m_to_k = block_map(c, s.pM, s.pK, false);
+  }
+
+  // triple lists of the step
+  triples_for(c, s, s.pS, false, s.pSinv, false, s.pSinv, false);   // S X
+  triples_for(c, s, s.pSinv, false, s.pSinv, false, s.pSinv, false);  // X Z
+  triples_for(c, s, s.pSinv, false, s.pH, false, s.pT, false);      // T = S^-1 H
+  triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);         // M = U K
+  triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);           // K' = M U^dagger
+  if (p.prop == RT_PROP_EM) {
+    triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);  // T^2
+    triples_for(c, s, s.pT, false, s.pU, false, s.pU, false);  // T^n
+  } else {
+    s.a_to_s = block_map(c, s.pA, s.pS, false);
+    s.a_to_h = block_map(c, s.pA, s.pH, false);
+    s.Acn = c->arena.get_n<double2>(nvals(s, s.pA));
+    s.Bcn = c->arena.get_n<double2>(nvals(s, s.pA));
+    s.X = c->arena.get_n<double2>(nvals(s, s.pU));
+    s.Xn = c->arena.get_n<double2>(nvals(s, s.pU));
+    s.Zc = c->arena.get_n<double2>(nvals(s, s.pU));
+    triples_for(c, s, s.pA, false, s.pU, false, s.pU, false);  // A X
+    triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);  // X Z
+    triples_for(c, s, s.pU, false, s.pA, false, s.pU, false);  // X B
+  }
+  if (p.precision == RT_FP32) {
+    RT_REQUIRE(p.r_M >= p.r_K, RT_EINVAL, "the FP32 delta-form sandwich needs r_M >= r_K");
+    s.dUf = c->arena.get_n<float2>(nvals(s, s.pU));
+    s.Kf = c->arena.get_n<float2>(nvals(s, s.pK));
+    s.Mf = c->arena.get_n<float2>(nvals(s, s.pM));
+    s.Wf = c->arena.get_n<float2>(nvals(s, s.pM));
+    if (p.prop == RT_PROP_EM) {
+      s.Tf = c->arena.get_n<float>(nvals(s, s.pT));
+      s.Pf0 = c->arena.get_n<float>(nvals(s, s.pU));
+      s.Pf1 = c->arena.get_n<float>(nvals(s, s.pU));
+      s.T0 = c->arena.get_n<double>(nvals(s, s.pT));
+      s.TD = c->arena.get_n<double>(nvals(s, s.pT));
+    }
+  }
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+}
+
+// ----------------------------------------------------------------------------
+// Hotelling inverse of S (Sec. V.A), cut to r_Sinv
+// ----------------------------------------------------------------------------
+static rt_status hotelling_sinv(rt_ctx* c, Sys& s) {
+  const rt_params& p = c->p;
+  Pattern* P = s.pSinv;
+  TripleInfo& tSX = triples_for(c, s, s.pS, false, P, false, P, false);
+  TripleInfo& tXZ = triples_for(c, s, P, false, P, false, P, false);
+  launch_inf_norm(s.S, s.pS->rowptr, s.pS->col, s.d_bsize, s.B, s.n_atoms, s.rows_tmp, s.scal, c->ws);
+  double nrm = 0.0;
+  RT_CUDA_CHECK(cudaMemcpyAsync(&nrm, s.scal, sizeof(double), cudaMemcpyDeviceToHost, c->ws));
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+  RT_REQUIRE(nrm > 0 && std::isfinite(nrm), RT_ENUMERIC, "||S||_inf is not a positive finite number");
+  launch_identity(s.Sinv, false, P->nnzb, P->rowidx, P->col, s.B, 1.0 / nrm, c->ws);
+  double prev = -1.0, res = 0.0;
+  int it = 0;
+  rt_status status = RT_OK;
+  s.sinv_status = "maxit";
+  for (;;) {
+    // Z = 2I - S X, residual ||I - S X||
+    GemmArgs g = args(s.S, s.Sinv, s.Zs);
+    g.red = s.red_items;
+    gemm(c, s, PC_MISC, tSX, false, false, false, false, EPI_TWO_I, g, P);
+    residual_from_items(c, s, tSX, s.scal, nullptr);
+    RT_CUDA_CHECK(cudaMemcpyAsync(&res, s.scal, sizeof(double), cudaMemcpyDeviceToHost, c->ws));
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    if (!std::isfinite(res) || res > 1.0) {
+      s.sinv_status = "diverged";
+      status = RT_ENOTCONV;
+      break;
+    }
+    if (res < p.hot_tol) {
+      s.sinv_status = "converged";
+      break;
+    }
+    if (prev >= 0.0 && res > 0.9 * prev) {
+      s.sinv_status = "stagnated";
+      break;
+    }
+    if (it >= p.hot_maxit) {
+      status = RT_ENOTCONV;
+      break;
+    }
+    // X <- X Z
+    gemm(c, s, PC_MISC, tXZ, false, false, false, false, EPI_STORE, args(s.Sinv, s.Zs, s.Xs2), P);
+    std::swap(s.Sinv, s.Xs2);
+    prev = res;
+    ++it;
+  }
+  s.sinv_iters = it;
+  s.sinv_resid = res;
+  s.sinv_ready = true;
+  if (s.X) launch_restrict(s.Sinv, (double*)s.X, s.u_to_sinv, s.pU->nnzb, s.B, 1, c->ws);
+  if (c->p.precision == RT_FP32 && c->p.prop == RT_PROP_EM) {
+    // T0 = cut(S^-1 H0) and T_D = cut(S^-1 D_dir): T(t) = T0 - E(t) T_D exactly
+    TripleInfo& tT = triples_for(c, s, P, false, s.pH, false, s.pT, false);
+    gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.H0, s.T0), s.pT);
+    gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.D[c->field.dir], s.TD), s.pT);
+  }
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+  c->graph_dirty = true;
+  return status;
+}
+
+// ----------------------------------------------------------------------------
+// propagator
+// ----------------------------------------------------------------------------
+static void taylor_coef(int n, double dt, double* mag, int* imag) {
+  // (-i dt)^n / n!: (-i)^n = 1, -i, -1, i for n mod 4 = 0..3
+  double v = 1.0;
+  for (int k = 1; k <= n; ++k) v *= dt / k;
+  switch (n % 4) {
+    case 0: *mag = v; *imag = 0; break;
+    case 1: *mag = -v; *imag = 1; break;
+    case 2: *mag = -v; *imag = 0; break;
+    default: *mag = v; *imag = 1; break;
+  }
+}
+
+// U = sum_{n<terms} c_n T^n with T real on P_T, powers cut to P_U.  FP64 U
+// (ident) or the FP32 difference dU = U - I.
+static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int terms, bool fp32_delta) {
+  TripleInfo& t2 = triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);
+  TripleInfo& tn = triples_for(c, s, s.pT, false, s.pU, false, s.pU, false);
+  double c1 = 0.0;
+  int c1i = 0;
+  taylor_coef(1, dt, &c1, &c1i);
+  if (!fp32_delta) {
+    run(c, PC_TAYLOR, 0, 0, [&] {
+      launch_taylor_init(s.U, false, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
+                         terms > 1 ? c1 : 0.0, c1i, 1, c->ws);
+    });
+    const double* prev = T;
+    double* bufs[2] = {s.P0, s.P1};
+    for (int n = 2; n < terms; ++n) {
+      double cn;
+      int ci;
+      taylor_coef(n, dt, &cn, &ci);
+      GemmArgs g = args(T, prev, bufs[n % 2]);
+      g.U = s.U;
+      g.coef = cn;
+      g.coef_imag = ci;
+      gemm(c, s, PC_TAYLOR, n == 2 ? t2 : tn, false, false, false, false, EPI_STORE_ACC, g, s.pU);
+      prev = bufs[n % 2];
+    }
+  } else {
+    run(c, PC_TAYLOR, 0, 0, [&] {
+      launch_d2f(T, s.Tf, (int64_t)nvals(s, s.pT), c->ws);
+      launch_taylor_init(s.dUf, true, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
+                         terms > 1 ? c1 : 0.0, c1i, 0, c->ws);
+    });
+    const float* prev = s.Tf;
+    float* bufs[2] = {s.Pf0, s.Pf1};
+    for (int n = 2; n < terms; ++n) {
+      double cn;
+      int ci;
+      taylor_coef(n, dt, &cn, &ci);
+      GemmArgs g = args(s.Tf, prev, bufs[n % 2]);
+      g.U = s.dUf;
+      g.coef = cn;
+      g.coef_imag = ci;
+      gemm(c, s, PC_TAYLOR, n == 2 ? t2 : tn, true, false, false, false, EPI_STORE_ACC, g, s.pU);
+      prev = bufs[n % 2];
+    }
+  }
+}
+
+static void build_propagator(rt_ctx* c, Sys& s) {
+  const rt_params& p = c->p;
+  const int dir = c->field.dir;
+  const bool fp32 = p.precision == RT_FP32;
+  if (p.prop == RT_PROP_EM) {
+    if (fp32) {
+      // T(t+dt/2) = T0 - E T_D (linearity of the cut product in E)
+      run(c, PC_FIELD, 0, 16.0 * nvals(s, s.pT),
+          [&] { launch_field_axpy(s.T0, s.TD, c->dstate, 1.0, s.T, (int64_t)nvals(s, s.pT), c->ws); });
+      taylor_series(c, s, s.T, p.dt, p.taylor_terms, true);
+    } else {
+      run(c, PC_FIELD, 0, 24.0 * nvals(s, s.pH),
+          [&] { launch_field_axpy(s.H0, s.D[dir], c->dstate, 1.0, s.Hm, (int64_t)nvals(s, s.pH), c->ws); });
+      TripleInfo& tT = triples_for(c, s, s.pSinv, false, s.pH, false, s.pT, false);
+      gemm(c, s, PC_T, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.Hm, s.T), s.pT);
+      taylor_series(c, s, s.T, p.dt, p.taylor_terms, false);
+    }
+  } else {
+    run(c, PC_FIELD, 0, 24.0 * nvals(s, s.pH),
+        [&] { launch_field_axpy(s.H0, s.D[dir], c->dstate, 1.0, s.Hm, (int64_t)nvals(s, s.pH), c->ws); });
+    run(c, PC_FIELD, 0, 48.0 * nvals(s, s.pA), [&] {
+      launch_cn_operands(s.S, s.a_to_s, s.Hm, s.a_to_h, 0.5 * p.dt, s.Acn, s.Bcn, s.pA->nnzb, s.B, c->ws);
+    });
+    TripleInfo& tAX = triples_for(c, s, s.pA, false, s.pU, false, s.pU, false);
+    TripleInfo& tXZ = triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);
+    TripleInfo& tXB = triples_for(c, s, s.pU, false, s.pA, false, s.pU, false);
+    // X alternates between two fixed buffers and ends in s.X, so that a
+    // captured step graph can be replayed (no host-side pointer swaps)
+    double2* xb[2] = {s.X, s.Xn};
+    for (int it = 0; it < p.hot_step_iters; ++it) {
+      double2* xi = xb[it % 2];
+      double2* xo = xb[(it + 1) % 2];
+      GemmArgs g = args(s.Acn, xi, s.Zc);
+      g.red = s.red_items;
+      gemm(c, s, PC_CN_HOT, tAX, false, true, false, false, EPI_TWO_I, g, s.pU);
+      if (it == p.hot_step_iters - 1) residual_from_items(c, s, tAX, s.scal + 1, nullptr);
+      gemm(c, s, PC_CN_HOT, tXZ, false, true, false, false, EPI_STORE, args(xi, s.Zc, xo), s.pU);
+    }
+    if (p.hot_step_iters % 2 == 1)
+      run(c, PC_MISC, 0, 0, [&] {
+        RT_CUDA_CHECK(cudaMemcpyAsync(s.X, s.Xn, sizeof(double2) * nvals(s, s.pU), cudaMemcpyDeviceToDevice, c->ws));
+      });
+    if (p.hot_step_iters > 0) run(c, PC_MISC, 0, 0, [&] { launch_set_hot(c->dstate, s.scal + 1, p.hot_step_iters, c->ws); });
+    gemm(c, s, PC_CN_U, tXB, false, true, false, false, EPI_STORE, args(s.X, s.Bcn, s.U), s.pU);
+    if (fp32) {
+      // dU = U - I in FP32 for the delta-form sandwich
+      run(c, PC_MISC, 0, 0,
+          [&] { launch_u_minus_i_f32(s.U, s.dUf, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws); });
+    }
+  }
+}
+
+
+// ----------------------------------------------------------------------------
+// sandwich K <- U K U^dagger and observables
+// ----------------------------------------------------------------------------
+static void sandwich(rt_ctx* c, Sys& s, int kick, int slot) {
+  const bool fp32 = c->p.precision == RT_FP32;
+  TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
+  TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
+  double2* K = s.K[kick];
+  unsigned long long* herm = &c->dstate->herm_bits[slot];
+  if (!fp32) {
+    gemm(c, s, PC_UK, tM, false, true, false, false, EPI_STORE, args(s.U, K, s.M), s.pM);
+    GemmArgs g = args(s.M, s.U, K);
+    g.herm_max = herm;
+    gemm(c, s, PC_MUDAG, tK, false, true, false, true, EPI_SANDWICH, g, s.pK);
+  } else {
+    // delta form: M = dU K, W = K + M, K' = K + M + W dU^dagger (K, sums in FP64)
+    run(c, PC_MISC, 0, 0, [&] { launch_d2f((const double*)K, (float*)s.Kf, 2 * (int64_t)nvals(s, s.pK), c->ws); });
+    gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUf, s.Kf, s.Mf), s.pM);
+    run(c, PC_MISC, 0, 0, [&] { launch_delta_w(K, s.m_to_k, s.Mf, s.Wf, s.pM->nnzb, s.B, c->ws); });
+    GemmArgs g = args(s.Wf, s.dUf, K);
+    g.herm_max = herm;
+    g.base = K;
+    g.addend = s.Mf;
+    g.add_map = s.k_to_m;
+    gemm(c, s, PC_MUDAG, tK, true, true, false, true, EPI_DELTA_SANDWICH, g, s.pK);
+  }
+}
+
+static void observe(rt_ctx* c, Sys& s, int kick, int slot) {
+  double bytes = 16.0 * nvals(s, s.pK) + 8.0 * 4 * nvals(s, s.pH);
+  run(c, PC_OBS, 0, bytes, [&] {
+    launch_traces(s.K[kick], s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S, s.k_to_sT, s.D[0], s.D[1],
+                  s.D[2], s.k_to_hT, s.red_part, c->dstate, slot, c->ring, c->p.obs_capacity, c->n_slots, slot,
+                  c->ws);
+  });
+}
+
+static void enqueue_step(rt_ctx* c) {
+  run(c, PC_MISC, 0, 0, [&] { launch_begin_step(c->dstate, c->field, c->p.dt, c->n_slots, c->ws); });
+  int slot = 0;
+  for (auto& sp : c->sys) {
+    Sys& s = *sp;
+    if (c->p.full_step) build_propagator(c, s);
+    for (int k = 0; k < c->p.n_kick; ++k) sandwich(c, s, k, slot + k);
+    slot += c->p.n_kick;
+  }
+  run(c, PC_MISC, 0, 0, [&] { launch_end_step(c->dstate, c->p.dt, c->ws); });
+  slot = 0;
+  for (auto& sp : c->sys) {
+    for (int k = 0; k < c->p.n_kick; ++k) observe(c, *sp, k, slot + k);
+    slot += c->p.n_kick;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// set-up helpers used by the API
+// ----------------------------------------------------------------------------
+static void reset_time(rt_ctx* c) {
+  DevState z;
+  memset(&z, 0, sizeof(z));
+  RT_CUDA_CHECK(cudaMemcpyAsync(c->dstate, &z, sizeof(DevState), cudaMemcpyHostToDevice, c->ws));
+  c->host_step = 0;
+  c->t_host = 0.0;
+  std::fill(c->read_upto.begin(), c->read_upto.end(), 0);
+}
+
+// K <- V K V^dagger with V = exp(+i kappa S^-1 D_dir) (Taylor, powers cut to r_U)
+static void kick_one(rt_ctx* c, Sys& s, int kick, int dir, double kappa) {
+  TripleInfo& tT = triples_for(c, s, s.pSinv, false, s.pH, false, s.pT, false);
+  gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.D[dir], s.T), s.pT);
+  taylor_series(c, s, s.T, -kappa, c->p.kick_terms, false);
+  TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
+  TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
+  gemm(c, s, PC_MISC, tM, false, true, false, false, EPI_STORE, args(s.U, s.K[kick], s.M), s.pM);
+  gemm(c, s, PC_MISC, tK, false, true, false, true, EPI_SANDWICH, args(s.M, s.U, s.K[kick]), s.pK);
+  s.u_ready = false;  // U now holds V
+}
+
+// K0 = f(S^-1 H0) S^-1 by a Chebyshev expansion (real FP64 on P_K)
+static void ground_state(rt_ctx* c, Sys& s, int order, double mu, double kT, double e_lo, double e_hi) {
+  RT_REQUIRE(order >= 0 && kT > 0 && e_hi > e_lo, RT_EINVAL, "bad ground-state parameters");
+  Pattern* PK = s.pK;
+  TripleInfo& tT = triples_for(c, s, s.pSinv, false, s.pH, false, s.pT, false);
+  TripleInfo& tTK = triples_for(c, s, s.pT, false, PK, false, PK, false);
+  gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.H0, s.T), s.pT);
+  // Chebyshev coefficients of the Fermi function (Chebyshev-Gauss quadrature)
+  const double a = 0.5 * (e_hi + e_lo), w = 0.5 * (e_hi - e_lo);
+  const int Mq = 4 * (order + 1);
+  std::vector<double> f(Mq), th(Mq), coef(order + 1);
+  for (int k = 0; k < Mq; ++k) {
+    th[k] = M_PI * (k + 0.5) / Mq;
+    double e = a + w * std::cos(th[k]);
+    f[k] = 0.5 * (1.0 - std::tanh(0.5 * (e - mu) / kT));
+  }
+  for (int n = 0; n <= order; ++n) {
+    double acc = 0.0;
+    for (int k = 0; k < Mq; ++k) acc += f[k] * std::cos(n * th[k]);
+    coef[n] = (n ? 2.0 : 1.0) / Mq * acc;
+  }
+  size_t nv = nvals(s, PK);
+  double* Y0 = c->arena.get_n<double>(nv);
+  double* Y1 = c->arena.get_n<double>(nv);
+  double* Y2 = c->arena.get_n<double>(nv);
+  double* TY = c->arena.get_n<double>(nv);
+  double* Kr = c->arena.get_n<double>(nv);
+  launch_restrict(s.Sinv, Y0, s.k_to_sinv, PK->nnzb, s.B, 0, c->ws);
+  RT_CUDA_CHECK(cudaMemcpyAsync(Kr, Y0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, c->ws));
+  launch_scale(Kr, coef[0], (int64_t)nv, c->ws);
+  double *Ym = Y0, *Yc = Y0, *Yn = Y1;
+  for (int n = 1; n <= order; ++n) {
+    gemm(c, s, PC_MISC, tTK, false, false, false, false, EPI_STORE, args(s.T, Yc, TY), PK);
+    launch_cheb_step(TY, Yc, Ym, Yn, Kr, a, w, coef[n], n == 1 ? 1 : 0, (int64_t)nv, c->ws);
+    // rotate: (Ym, Yc) <- (Yc, Yn); Yn <- a free buffer
+    double* freeb = (n == 1) ? Y2 : Ym;
+    Ym = Yc;
+    Yc = Yn;
+    Yn = freeb;
+  }
+  for (size_t k = 0; k < s.K.size(); ++k)
+    launch_symmetrise_to_complex(Kr, s.K[k], PK->nnzb, PK->rowidx, PK->col, PK->tmap, s.d_bsize, s.B, c->ws);
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+}
+
+static void ensure_unitarity_lists(rt_ctx* c, Sys& s) {
+  if (s.pW) return;
+  double rW = c->p.r_U + std::max(s.r_S, 1e-9);
+  s.pW = pattern_for(c, s, rW);
+  s.Sc = c->arena.get_n<double2>(nvals(s, s.pS));
+  int32_t* ident = c->arena.get_n<int32_t>(s.pS->nnzb);
+  std::vector<int32_t> h(s.pS->nnzb);
+  for (int64_t q = 0; q < s.pS->nnzb; ++q) h[q] = (int32_t)q;
+  RT_CUDA_CHECK(cudaMemcpyAsync(ident, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, c->ws));
+  launch_restrict(s.S, (double*)s.Sc, ident, s.pS->nnzb, s.B, 1, c->ws);
+  s.W = c->arena.get_n<double2>(nvals(s, s.pW));
+  s.E = c->arena.get_n<double2>(nvals(s, s.pU));
+  s.u_to_s = block_map(c, s.pU, s.pS, false);
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+}
+
+static void unitarity(rt_ctx* c, Sys& s, int metric, double* mx, double* mean) {
+  ensure_unitarity_lists(c, s);
+  if (metric) {
+    TripleInfo& tW = triples_for(c, s, s.pS, false, s.pU, false, s.pW, false);
+    TripleInfo& tE = triples_for(c, s, s.pU, true, s.pW, false, s.pU, false);
+    gemm(c, s, PC_MISC, tW, false, true, false, false, EPI_STORE, args(s.Sc, s.U, s.W), s.pW);
+    gemm(c, s, PC_MISC, tE, false, true, true, false, EPI_STORE, args(s.U, s.W, s.E), s.pU);
+  } else {
+    TripleInfo& tE = triples_for(c, s, s.pU, true, s.pU, false, s.pU, false);
+    gemm(c, s, PC_MISC, tE, false, true, true, false, EPI_STORE, args(s.U, s.U, s.E), s.pU);
+  }
+  double* pmax = c->arena.get_n<double>(1024);
+  double* psum = c->arena.get_n<double>(1024);
+  int nb = launch_unitarity_dev(s.E, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.d_bsize, s.B, metric ? s.S : nullptr,
+                                metric ? s.u_to_s : nullptr, pmax, psum, c->ws);
+  std::vector<double> hm(nb), hs(nb);
+  RT_CUDA_CHECK(cudaMemcpyAsync(hm.data(), pmax, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->ws));
+  RT_CUDA_CHECK(cudaMemcpyAsync(hs.data(), psum, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->ws));
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+  double m = 0.0, sm = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    m = std::max(m, hm[i]);
+    sm += hs[i];
+  }
+  int64_t cnt = 0;
+  for (int i = 0; i < s.n_atoms; ++i)
+    for (int q = s.pU->h_rowptr[i]; q < s.pU->h_rowptr[i + 1]; ++q)
+      cnt += (int64_t)s.bsize[i] * s.bsize[s.pU->h_col[q]];
+  *mx = m;
+  *mean = cnt ? sm / (double)cnt : 0.0;
+}
+
+static Pattern* pattern_by_id(Sys& s, int which) {
+  switch (which) {
+    case RT_PAT_S: return s.pS;
+    case RT_PAT_H: return s.pH;
+    case RT_PAT_SINV: return s.pSinv;
+    case RT_PAT_T: return s.pT;
+    case RT_PAT_U: return s.pU;
+    case RT_PAT_K: return s.pK;
+    case RT_PAT_M: return s.pM;
+    case RT_PAT_A: return s.pA;
+    case RT_PAT_W: return s.pW;
+    default: return nullptr;
+  }
+}
+
+// (pattern, device values, complex?) of a readable matrix
+static void matrix_by_id(rt_ctx* c, Sys& s, int kick, int which, Pattern** P, const void** v, bool* cplx) {
+  *cplx = false;
+  switch (which) {
+    case RT_MAT_S: *P = s.pS; *v = s.S; return;
+    case RT_MAT_H0: *P = s.pH; *v = s.H0; return;
+    case RT_MAT_DX: *P = s.pH; *v = s.D[0]; return;
+    case RT_MAT_DY: *P = s.pH; *v = s.D[1]; return;
+    case RT_MAT_DZ: *P = s.pH; *v = s.D[2]; return;
+    case RT_MAT_SINV: *P = s.pSinv; *v = s.Sinv; return;
+    case RT_MAT_T: *P = s.pT; *v = s.T; return;
+    case RT_MAT_U: *P = s.pU; *v = s.U; *cplx = true; return;
+    case RT_MAT_K:
+      RT_REQUIRE(kick >= 0 && kick < c->p.n_kick, RT_EINVAL, "kick index out of range");
+      *P = s.pK; *v = s.K[kick]; *cplx = true; return;
+    case RT_MAT_X:
+      RT_REQUIRE(s.X != nullptr, RT_EINVAL, "X exists only in the Crank-Nicolson mode");
+      *P = s.pU; *v = s.X; *cplx = true; return;
+    default: throw Error{RT_EINVAL, "unknown matrix id"};
+  }
+}
+
+static int64_t true_elems(const Sys& s, const Pattern* P) {
+  int64_t n = 0;
+  for (int i = 0; i < s.n_atoms; ++i)
+    for (int q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) n += (int64_t)s.bsize[i] * s.bsize[P->h_col[q]];
+  return n;
+}
+
+}  // namespace rt
+
+// ============================================================================
+// C ABI
+// ============================================================================
+using namespace rt;
+
+template <class F>
+static rt_status guarded(rt_ctx* c, F&& f) {
+  if (!c) return RT_EINVAL;
+  if (c->poisoned) return RT_ESTATE;
+  c->err.clear();
+  try {
+    RT_CUDA_CHECK(cudaEventRecord(c->ev_in, c->user));
+    RT_CUDA_CHECK(cudaStreamWaitEvent(c->ws, c->ev_in, 0));
+    rt_status st = f();
+    RT_CUDA_CHECK(cudaEventRecord(c->ev_out, c->ws));
+    RT_CUDA_CHECK(cudaStreamWaitEvent(c->user, c->ev_out, 0));
+    return st;
+  } catch (const Error& e) {
+    c->err = e.msg;
+    if (e.code == RT_ECUDA || e.code == RT_ETIMEOUT || e.code == RT_EINTERNAL) c->poisoned = true;
+    return e.code;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    c->poisoned = true;
+    return RT_EINTERNAL;
+  }
+}
+
+static rt_status check_sys(rt_ctx* c, int32_t sys) {
+  if (sys < 0 || sys >= (int32_t)c->sys.size()) throw Error{RT_EINVAL, "system index out of range"};
+  return RT_OK;
+}
+
+extern "C" {
+
+rt_status rt_default_params(rt_params* p) {
+  if (!p) return RT_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->r_Sinv = p->r_T = p->r_U = p->r_K = p->r_M = 8.0;
+  p->dt = 0.05;
+  p->prop = RT_PROP_EM;
+  p->taylor_terms = 6;
+  p->hot_tol = 1e-10;
+  p->hot_maxit = 100;
+  p->hot_step_iters = 2;
+  p->precision = RT_FP64;
+  p->full_step = 1;
+  p->n_kick = 1;
+  p->kick_terms = 12;
+  p->obs_capacity = 4096;
+  p->use_graph = 1;
+  return RT_OK;
+}
+
+rt_status rt_create(rt_ctx** out, const rt_system* sys, int32_t n_sys, const rt_params* p, void* cuda_stream,
+                    rt_alloc_fn alloc, rt_free_fn free_fn, void* alloc_user) {
+  if (!out) return RT_EINVAL;
+  *out = nullptr;
+  auto* c = new rt_ctx();
+  c->alloc.alloc = alloc;
+  c->alloc.free = free_fn;
+  c->alloc.user = alloc_user;
+  c->arena.alloc = &c->alloc;
+  c->user = (cudaStream_t)cuda_stream;
+  try {
+    RT_REQUIRE(sys && n_sys > 0 && p, RT_EINVAL, "need at least one system and params");
+    c->p = *p;
+    const rt_params& q = c->p;
+    RT_REQUIRE(q.r_Sinv > 0 && q.r_T > 0 && q.r_U > 0 && q.r_K > 0 && q.r_M > 0, RT_EINVAL, "radii must be positive");
+    RT_REQUIRE(q.dt > 0 && std::isfinite(q.dt), RT_EINVAL, "dt must be positive");
+    RT_REQUIRE(q.prop == RT_PROP_EM || q.prop == RT_PROP_CN, RT_EINVAL, "prop must be RT_PROP_EM or RT_PROP_CN");
+    RT_REQUIRE(q.taylor_terms >= 1 && q.taylor_terms <= 32, RT_EINVAL, "taylor_terms must be in 1..32");
+    RT_REQUIRE(q.precision == RT_FP64 || q.precision == RT_FP32, RT_EINVAL, "precision must be RT_FP64 or RT_FP32");
+    RT_REQUIRE(q.n_kick >= 1 && q.n_kick <= 3, RT_EINVAL, "n_kick must be in 1..3");
+    RT_REQUIRE(q.obs_capacity >= 1, RT_EINVAL, "obs_capacity must be positive");
+    RT_REQUIRE(q.hot_step_iters >= 0 && q.hot_maxit >= 0 && q.kick_terms >= 1, RT_EINVAL, "bad iteration counts");
+    RT_REQUIRE((int64_t)n_sys * q.n_kick <= RT_MAX_SLOTS, RT_EINVAL, "too many (system, kick) pairs");
+    RT_CUDA_CHECK(cudaStreamCreateWithFlags(&c->ws, cudaStreamNonBlocking));
+    RT_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    RT_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    c->arena.stream = c->ws;
+    RT_CUDA_CHECK(cudaEventRecord(c->ev_in, c->user));
+    RT_CUDA_CHECK(cudaStreamWaitEvent(c->ws, c->ev_in, 0));
+    c->n_slots = n_sys * q.n_kick;
+    c->read_upto.assign(c->n_slots, 0);
+    c->dstate = c->arena.get_n<DevState>(1);
+    c->ring = c->arena.get_n<double>((size_t)q.obs_capacity * c->n_slots * RT_NOBS);
+    RT_CUDA_CHECK(cudaMemsetAsync(c->ring, 0, sizeof(double) * (size_t)q.obs_capacity * c->n_slots * RT_NOBS, c->ws));
+    reset_time(c);
+    for (int i = 0; i < n_sys; ++i) {
+      c->sys.push_back(std::make_unique<Sys>());
+      setup_system(c, *c->sys.back(), sys[i]);
+    }
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+  } catch (const Error& e) {
+    if (c->ws) cudaStreamSynchronize(c->ws);
+    c->arena.release_all();
+    if (c->ws) cudaStreamDestroy(c->ws);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    rt_status code = e.code;
+    // keep the message reachable through a static buffer for the failed create
+    static thread_local std::string last;
+    last = e.msg;
+    fprintf(stderr, "rt_create: %s\n", e.msg.c_str());
+    delete c;
+    return code;
+  }
+  *out = c;
+  return RT_OK;
+}
+
+rt_status rt_set_field(rt_ctx* c, const rt_field* f) {
+  return guarded(c, [&] {
+    RT_REQUIRE(f, RT_EINVAL, "NULL field");
+    RT_REQUIRE(f->dir >= 0 && f->dir < 3, RT_EINVAL, "field dir must be 0, 1 or 2");
+    RT_REQUIRE(f->kind >= RT_FIELD_NONE && f->kind <= RT_FIELD_CONSTANT, RT_EINVAL, "unknown field kind");
+    if (f->kind == RT_FIELD_GAUSSIAN) RT_REQUIRE(f->sigma > 0, RT_EINVAL, "sigma must be positive");
+    bool dir_changed = f->dir != c->field.dir;
+    c->field.kind = f->kind;
+    c->field.dir = f->dir;
+    c->field.E0 = f->E0;
+    c->field.t0 = f->t0;
+    c->field.sigma = f->sigma;
+    c->field.omega = f->omega;
+    c->graph_dirty = true;
+    if (dir_changed && c->p.precision == RT_FP32 && c->p.prop == RT_PROP_EM) {
+      for (auto& sp : c->sys) {
+        Sys& s = *sp;
+        if (!s.sinv_ready) continue;
+        TripleInfo& tT = triples_for(c, s, s.pSinv, false, s.pH, false, s.pT, false);
+        gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.D[c->field.dir], s.TD), s.pT);
+      }
+    }
+    return RT_OK;
+  });
+}
+
+rt_status rt_inverse(rt_ctx* c, int32_t sys, int32_t* iters, double* residual) {
+  return guarded(c, [&] {
+    if (sys >= 0) check_sys(c, sys);
+    rt_status worst = RT_OK;
+    for (size_t i = 0; i < c->sys.size(); ++i) {
+      rt_status st = hotelling_sinv(c, *c->sys[i]);
+      if (st != RT_OK) {
+        worst = st;
+        c->err = "Hotelling " + c->sys[i]->sinv_status + " for system " + std::to_string(i) +
+                 " (residual " + std::to_string(c->sys[i]->sinv_resid) + ")";
+      }
+    }
+    int32_t k = sys >= 0 ? sys : 0;
+    if (iters) *iters = c->sys[k]->sinv_iters;
+    if (residual) *residual = c->sys[k]->sinv_resid;
+    return worst;
+  });
+}
+
+rt_status rt_set_density(rt_ctx* c, int32_t sys, int32_t kick, const double* h) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    RT_REQUIRE(kick >= 0 && kick < c->p.n_kick, RT_EINVAL, "kick index out of range");
+    RT_REQUIRE(h, RT_EINVAL, "NULL density");
+    Sys& s = *c->sys[sys];
+    const Pattern& P = *s.pK;
+    const int B = s.B;
+    std::vector<double> buf(2 * (size_t)P.nnzb * B * B, 0.0);
+    size_t o = 0;
+    for (int i = 0; i < s.n_atoms; ++i)
+      for (int q = P.h_rowptr[i]; q < P.h_rowptr[i + 1]; ++q) {
+        int j = P.h_col[q];
+        int bi = s.bsize[i], bj = s.bsize[j];
+        double* blk = buf.data() + 2 * (size_t)q * B * B;
+        for (int a = 0; a < bi; ++a)
+          for (int b = 0; b < bj; ++b) {
+            blk[2 * (a * B + b)] = h[2 * (o + (size_t)a * bj + b)];
+            blk[2 * (a * B + b) + 1] = h[2 * (o + (size_t)a * bj + b) + 1];
+          }
+        o += (size_t)bi * bj;
+      }
+    RT_CUDA_CHECK(cudaMemcpyAsync(s.K[kick], buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->ws));
+    reset_time(c);
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    return RT_OK;
+  });
+}
+
+rt_status rt_ground_state(rt_ctx* c, int32_t sys, int32_t order, double mu, double kT, double e_lo, double e_hi) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    Sys& s = *c->sys[sys];
+    RT_REQUIRE(s.sinv_ready, RT_ESTATE, "call rt_inverse first");
+    ground_state(c, s, order, mu, kT, e_lo, e_hi);
+    reset_time(c);
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    return RT_OK;
+  });
+}
+
+rt_status rt_kick(rt_ctx* c, int32_t sys, int32_t kick, int32_t dir, double kappa) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    RT_REQUIRE(kick >= 0 && kick < c->p.n_kick, RT_EINVAL, "kick index out of range");
+    RT_REQUIRE(dir >= 0 && dir < 3, RT_EINVAL, "dir must be 0, 1 or 2");
+    RT_REQUIRE(std::isfinite(kappa), RT_EINVAL, "kappa must be finite");
+    Sys& s = *c->sys[sys];
+    RT_REQUIRE(s.sinv_ready, RT_ESTATE, "call rt_inverse first");
+    kick_one(c, s, kick, dir, kappa);
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    return RT_OK;
+  });
+}
+
+rt_status rt_propagator(rt_ctx* c, double t) {
+  return guarded(c, [&] {
+    for (auto& sp : c->sys) RT_REQUIRE(sp->sinv_ready, RT_ESTATE, "call rt_inverse first");
+    // field at t + dt/2 through the device state
+    DevState tmp;
+    RT_CUDA_CHECK(cudaMemcpyAsync(&tmp, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->ws));
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    double t_saved = tmp.t;
+    tmp.t = t;
+    RT_CUDA_CHECK(cudaMemcpyAsync(c->dstate, &tmp, sizeof(DevState), cudaMemcpyHostToDevice, c->ws));
+    launch_begin_step(c->dstate, c->field, c->p.dt, c->n_slots, c->ws);
+    for (auto& sp : c->sys) {
+      build_propagator(c, *sp);
+      sp->u_ready = true;
+    }
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    RT_CUDA_CHECK(cudaMemcpyAsync(&tmp, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->ws));
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    tmp.t = t_saved;
+    RT_CUDA_CHECK(cudaMemcpyAsync(c->dstate, &tmp, sizeof(DevState), cudaMemcpyHostToDevice, c->ws));
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    c->graph_dirty = true;
+    return RT_OK;
+  });
+}
+
+rt_status rt_step(rt_ctx* c, int32_t n) {
+  return guarded(c, [&] {
+    RT_REQUIRE(n >= 0, RT_EINVAL, "n must be non-negative");
+    for (auto& sp : c->sys) {
+      RT_REQUIRE(sp->sinv_ready, RT_ESTATE, "call rt_inverse first");
+      if (!c->p.full_step) RT_REQUIRE(sp->u_ready, RT_ESTATE, "call rt_propagator first (full_step = 0)");
+    }
+    if (n == 0) return RT_OK;
+    if (c->profiling || !c->p.use_graph) {
+      for (int i = 0; i < n; ++i) enqueue_step(c);
+      if (c->profiling) collect_profile(c);
+    } else {
+      if (c->graph_dirty || !c->gexec) {
+        if (c->gexec) {
+          cudaGraphExecDestroy(c->gexec);
+          c->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        RT_CUDA_CHECK(cudaStreamBeginCapture(c->ws, cudaStreamCaptureModeThreadLocal));
+        try {
+          enqueue_step(c);
+        } catch (...) {
+          cudaStreamEndCapture(c->ws, &graph);
+          if (graph) cudaGraphDestroy(graph);
+          throw;
+        }
+        RT_CUDA_CHECK(cudaStreamEndCapture(c->ws, &graph));
+        cudaError_t e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        RT_CUDA_CHECK(e);
+        c->graph_dirty = false;
+      }
+      for (int i = 0; i < n; ++i) RT_CUDA_CHECK(cudaGraphLaunch(c->gexec, c->ws));
+    }
+    c->host_step += n;
+    c->t_host += n * c->p.dt;
+    return RT_OK;
+  });
+}
+
+rt_status rt_observables(rt_ctx* c, int32_t sys, int32_t kick, double* out, int32_t max_steps, int32_t* n_out) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    RT_REQUIRE(kick >= 0 && kick < c->p.n_kick, RT_EINVAL, "kick index out of range");
+    RT_REQUIRE(out && n_out && max_steps >= 0, RT_EINVAL, "bad output buffer");
+    int slot = sys * c->p.n_kick + kick;
+    int64_t cap = c->p.obs_capacity;
+    int64_t first = std::max(c->read_upto[slot], c->host_step - cap);
+    int64_t cnt = std::min<int64_t>(c->host_step - first, max_steps);
+    std::vector<double> ring((size_t)cap * c->n_slots * RT_NOBS);
+    RT_CUDA_CHECK(cudaMemcpyAsync(ring.data(), c->ring, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost, c->ws));
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    bool bad = false;
+    for (int64_t k = 0; k < cnt; ++k) {
+      int64_t r = (first + k) % cap;
+      const double* rec = ring.data() + (r * c->n_slots + slot) * RT_NOBS;
+      for (int v = 0; v < RT_NOBS; ++v) {
+        out[k * RT_NOBS + v] = rec[v];
+        if (!std::isfinite(rec[v])) bad = true;
+      }
+    }
+    c->read_upto[slot] = first + cnt;
+    *n_out = (int32_t)cnt;
+    if (bad) {
+      c->err = "NaN/Inf in an observable";
+      return RT_ENUMERIC;
+    }
+    return RT_OK;
+  });
+}
+
+rt_status rt_pattern_size(rt_ctx* c, int32_t sys, int32_t which, int64_t* nnzb) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    Sys& s = *c->sys[sys];
+    if (which == RT_PAT_W) ensure_unitarity_lists(c, s);
+    Pattern* P = pattern_by_id(s, which);
+    RT_REQUIRE(P && nnzb, RT_EINVAL, "unknown pattern id");
+    *nnzb = P->nnzb;
+    return RT_OK;
+  });
+}
+
+rt_status rt_get_pattern(rt_ctx* c, int32_t sys, int32_t which, int32_t* rowptr, int32_t* col) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    Sys& s = *c->sys[sys];
+    if (which == RT_PAT_W) ensure_unitarity_lists(c, s);
+    Pattern* P = pattern_by_id(s, which);
+    RT_REQUIRE(P && rowptr && col, RT_EINVAL, "unknown pattern id or NULL output");
+    std::memcpy(rowptr, P->h_rowptr.data(), sizeof(int32_t) * (s.n_atoms + 1));
+    if (P->nnzb) std::memcpy(col, P->h_col.data(), sizeof(int32_t) * P->nnzb);
+    return RT_OK;
+  });
+}
+
+rt_status rt_matrix_size(rt_ctx* c, int32_t sys, int32_t which, int64_t* n) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    Sys& s = *c->sys[sys];
+    Pattern* P;
+    const void* v;
+    bool cplx;
+    matrix_by_id(c, s, 0, which, &P, &v, &cplx);
+    RT_REQUIRE(n, RT_EINVAL, "NULL output");
+    *n = 2 * true_elems(s, P);
+    return RT_OK;
+  });
+}
+
+rt_status rt_get_matrix(rt_ctx* c, int32_t sys, int32_t kick, int32_t which, double* vals, int64_t capacity) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    Sys& s = *c->sys[sys];
+    Pattern* P;
+    const void* v;
+    bool cplx;
+    matrix_by_id(c, s, kick, which, &P, &v, &cplx);
+    RT_REQUIRE(vals, RT_EINVAL, "NULL output");
+    int64_t need = 2 * true_elems(s, P);
+    RT_REQUIRE(capacity >= need, RT_EINVAL, "output buffer too small");
+    const int B = s.B;
+    size_t nv = (size_t)P->nnzb * B * B * (cplx ? 2 : 1);
+    std::vector<double> buf(nv);
+    if (nv) RT_CUDA_CHECK(cudaMemcpyAsync(buf.data(), v, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->ws));
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    size_t o = 0;
+    for (int i = 0; i < s.n_atoms; ++i)
+      for (int q = P->h_rowptr[i]; q < P->h_rowptr[i + 1]; ++q) {
+        int j = P->h_col[q];
+        int bi = s.bsize[i], bj = s.bsize[j];
+        for (int a = 0; a < bi; ++a)
+          for (int b = 0; b < bj; ++b) {
+            size_t e = (size_t)q * B * B + a * B + b;
+            vals[2 * o] = cplx ? buf[2 * e] : buf[e];
+            vals[2 * o + 1] = cplx ? buf[2 * e + 1] : 0.0;
+            ++o;
+          }
+      }
+    return RT_OK;
+  });
+}
+
+rt_status rt_unitarity(rt_ctx* c, int32_t sys, int32_t metric_S, double* maxabs, double* meanabs) {
+  return guarded(c, [&] {
+    check_sys(c, sys);
+    RT_REQUIRE(maxabs && meanabs, RT_EINVAL, "NULL output");
+    Sys& s = *c->sys[sys];
+    RT_REQUIRE(c->p.precision == RT_FP64 || s.u_ready || c->p.prop == RT_PROP_CN, RT_ESTATE,
+               "no FP64 propagator held (FP32 EM keeps U - I in FP32)");
+    unitarity(c, s, metric_S ? 1 : 0, maxabs, meanabs);
+    return RT_OK;
+  });
+}
+
+rt_status rt_step_work(rt_ctx* c, double* flops, double* bytes) {
+  return guarded(c, [&] {
+    RT_REQUIRE(flops && bytes, RT_EINVAL, "NULL output");
+    c->counting = true;
+    c->count_flops = c->count_bytes = 0.0;
+    try {
+      enqueue_step(c);
+    } catch (...) {
+      c->counting = false;
+      throw;
+    }
+    c->counting = false;
+    *flops = c->count_flops;
+    *bytes = c->count_bytes;
+    return RT_OK;
+  });
+}
+
+rt_status rt_profile(rt_ctx* c, int32_t enable) {
+  return guarded(c, [&] {
+    c->profiling = enable != 0;
+    for (auto& pr : c->prof) pr = rt_ctx::Prof{};
+    return RT_OK;
+  });
+}
+
+rt_status rt_profile_read(rt_ctx* c, int32_t max, int32_t* n_classes, int64_t* launches, double* ms, double* flops,
+                          double* bytes, char* names) {
+  return guarded(c, [&] {
+    RT_REQUIRE(n_classes && launches && ms && flops && bytes && names, RT_EINVAL, "NULL output");
+    collect_profile(c);
+    int n = std::min<int>(max, PC_N);
+    for (int i = 0; i < n; ++i) {
+      launches[i] = c->prof[i].launches;
+      ms[i] = c->prof[i].ms;
+      flops[i] = c->prof[i].flops;
+      bytes[i] = c->prof[i].bytes;
+      std::snprintf(names + 32 * i, 32, "%s", kProfNames[i]);
+    }
+    *n_classes = n;
+    return RT_OK;
+  });
+}
+
+struct StateHeader {
+  uint64_t magic;
+  int64_t host_step;
+  double t_host;
+  int64_t n_slots;
+};
+
+rt_status rt_get_state(rt_ctx* c, void* buf, size_t* bytes) {
+  return guarded(c, [&] {
+    RT_REQUIRE(bytes, RT_EINVAL, "NULL size");
+    size_t need = sizeof(StateHeader) + sizeof(DevState) + sizeof(int64_t) * c->n_slots;
+    for (auto& sp : c->sys) {
+      Sys& s = *sp;
+      need += sizeof(double2) * nvals(s, s.pK) * s.K.size();
+      need += sizeof(double2) * nvals(s, s.pU);
+      if (s.X) need += sizeof(double2) * nvals(s, s.pU);
+    }
+    if (!buf) {
+      *bytes = need;
+      return RT_OK;
+    }
+    RT_REQUIRE(*bytes >= need, RT_EINVAL, "state buffer too small");
+    char* o = (char*)buf;
+    StateHeader h{0x52544b53544154ull, c->host_step, c->t_host, c->n_slots};
+    memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    RT_CUDA_CHECK(cudaMemcpyAsync(o, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->ws));
+    o += sizeof(DevState);
+    memcpy(o, c->read_upto.data(), sizeof(int64_t) * c->n_slots);
+    o += sizeof(int64_t) * c->n_slots;
+    for (auto& sp : c->sys) {
+      Sys& s = *sp;
+      for (double2* K : s.K) {
+        size_t nb = sizeof(double2) * nvals(s, s.pK);
+        RT_CUDA_CHECK(cudaMemcpyAsync(o, K, nb, cudaMemcpyDeviceToHost, c->ws));
+        o += nb;
+      }
+      size_t nu = sizeof(double2) * nvals(s, s.pU);
+      RT_CUDA_CHECK(cudaMemcpyAsync(o, s.U, nu, cudaMemcpyDeviceToHost, c->ws));
+      o += nu;
+      if (s.X) {
+        RT_CUDA_CHECK(cudaMemcpyAsync(o, s.X, nu, cudaMemcpyDeviceToHost, c->ws));
+        o += nu;
+      }
+    }
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    *bytes = need;
+    return RT_OK;
+  });
+}
+
+rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
+  if (!c) return RT_EINVAL;
+  c->poisoned = false;  // restoring a checkpoint clears the poisoned state
+  return guarded(c, [&] {
+    RT_REQUIRE(buf, RT_EINVAL, "NULL state");
+    size_t need = sizeof(StateHeader) + sizeof(DevState) + sizeof(int64_t) * c->n_slots;
+    for (auto& sp : c->sys) {
+      Sys& s = *sp;
+      need += sizeof(double2) * nvals(s, s.pK) * s.K.size() + sizeof(double2) * nvals(s, s.pU);
+      if (s.X) need += sizeof(double2) * nvals(s, s.pU);
+    }
+    RT_REQUIRE(bytes == need, RT_EINVAL, "state size does not match this context");
+    const char* o = (const char*)buf;
+    StateHeader h;
+    memcpy(&h, o, sizeof(h));
+    RT_REQUIRE(h.magic == 0x52544b53544154ull && h.n_slots == c->n_slots, RT_EINVAL, "not a state of this context");
+    o += sizeof(h);
+    RT_CUDA_CHECK(cudaMemcpyAsync(c->dstate, o, sizeof(DevState), cudaMemcpyHostToDevice, c->ws));
+    o += sizeof(DevState);
+    memcpy(c->read_upto.data(), o, sizeof(int64_t) * c->n_slots);
+    o += sizeof(int64_t) * c->n_slots;
+    for (auto& sp : c->sys) {
+      Sys& s = *sp;
+      for (double2* K : s.K) {
+        size_t nb = sizeof(double2) * nvals(s, s.pK);
+        RT_CUDA_CHECK(cudaMemcpyAsync(K, o, nb, cudaMemcpyHostToDevice, c->ws));
+        o += nb;
+      }
+      size_t nu = sizeof(double2) * nvals(s, s.pU);
+      RT_CUDA_CHECK(cudaMemcpyAsync(s.U, o, nu, cudaMemcpyHostToDevice, c->ws));
+      o += nu;
+      if (s.X) {
+        RT_CUDA_CHECK(cudaMemcpyAsync(s.X, o, nu, cudaMemcpyHostToDevice, c->ws));
+        o += nu;
+      }
+      if (c->p.precision == RT_FP32 && s.dUf)
+        launch_u_minus_i_f32(s.U, s.dUf, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
+    }
+    c->host_step = h.host_step;
+    c->t_host = h.t_host;
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    return RT_OK;
+  });
+}
+
+rt_status rt_synchronize(rt_ctx* c) {
+  return guarded(c, [&] {
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    return RT_OK;
+  });
+}
+
+const char* rt_last_error(rt_ctx* c) {
+  if (!c) return "NULL context";
+  return c->err.c_str();
+}
+
+void rt_destroy(rt_ctx* c) {
+  if (!c) return;
+  if (c->ws) cudaStreamSynchronize(c->ws);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto& pe : c->pending) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  for (auto& e : c->ev_free) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  c->arena.release_all();
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->ws) cudaStreamDestroy(c->ws);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Declarations of the elementwise / reduction launches (elementwise.cu).
+#pragma once
+
+#include "rt_internal.cuh"
+
+namespace rt {
+
+struct FieldParams {
+  int kind = RT_FIELD_NONE;
+  int dir = 0;
+  double E0 = 0.0, t0 = 0.0, sigma = 1.0, omega = 0.0;
+};
+
+// Device-resident step state (read by kernels so that a captured step graph
+// can be replayed without new kernel arguments).
+constexpr int RT_MAX_SLOTS = 256;  // (system, kick) pairs
+struct DevState {
+  int64_t step;
+  double t;
+  double E_mid;
+  double hot_resid;
+  int hot_iters;
+  int pad;
+  unsigned long long herm_bits[RT_MAX_SLOTS];
+};
+
+void launch_begin_step(DevState* s, const FieldParams& f, double dt, int n_herm, cudaStream_t st);
+void launch_end_step(DevState* s, double dt, cudaStream_t st);
+void launch_field_axpy(const double* H0, const double* D, const DevState* s, double scale, double* Hm, int64_t n,
+                       cudaStream_t st);
+void launch_taylor_init(void* U, bool fp32, int64_t nnzb_u, const int32_t* u_rowidx, const int32_t* u_col,
+                        const void* T, bool t_fp32, const int32_t* u_to_t, int B, double c1, int c1_imag, int ident,
+                        cudaStream_t st);
+void launch_identity(double* X, bool cplx, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B,
+                     double scale, cudaStream_t st);
+void launch_restrict(const double* src, double* dst, const int32_t* map, int64_t nnzb_dst, int B, int mode,
+                     cudaStream_t st);
+void launch_cn_operands(const double* S, const int32_t* a_to_s, const double* H, const int32_t* a_to_h, double c,
+                        double2* A, double2* Bm, int64_t nnzb_a, int B, cudaStream_t st);
+int reduce_blocks(int64_t n);
+void launch_sum(const double* v, int64_t n, double* part, double sqrt_div, double* out, double* out2,
+                cudaStream_t st);
+void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const int32_t* col, const int32_t* bsize,
+                   int B, const double* S, const int32_t* ks_map, const double* Dx, const double* Dy,
+                   const double* Dz, const int32_t* kd_map, double* part, const DevState* st, int herm_slot,
+                   double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s);
+int launch_unitarity_dev(const double2* E, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
+                         const int32_t* bsize, int B, const double* S, const int32_t* us_map, double* part_max,
+                         double* part_sum, cudaStream_t st);
+void launch_inf_norm(const double* S, const int32_t* rowptr, const int32_t* col, const int32_t* bsize, int B,
+                     int n_atoms, double* rows_tmp, double* out, cudaStream_t st);
+void launch_cheb_step(const double* TY, const double* Y, const double* Yp, double* Yn, double* Kacc, double a,
+                      double w, double c, int first, int64_t n, cudaStream_t st);
+void launch_scale(double* v, double c, int64_t n, cudaStream_t st);
+void launch_symmetrise_to_complex(const double* Kr, double2* K, int64_t nnzb, const int32_t* rowidx,
+                                  const int32_t* col, const int32_t* tmap, const int32_t* bsize, int B,
+                                  cudaStream_t st);
+void launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st);
+void launch_delta_w(const double2* K, const int32_t* m_to_k, const float2* Mf, float2* Wf, int64_t nnzb_m, int B,
+                    cudaStream_t st);
+void launch_set_hot(DevState* s, const double* resid, int iters, cudaStream_t st);
+void launch_u_minus_i_f32(const double2* U, float2* dU, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
+                          int B, cudaStream_t st);
+
+}  // namespace rt
