@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark: density-matrix RT-TDDFT steps per second on GB300.
+
+Workload: 4096-atom periodic diamond cell (8x8x8 conventional cells, a = 5.43 A,
+jitter 0.05 A), 13 functions per atom (n = 53,248), r_S = r_H = 7 A, truncation
+radii r_Sinv = r_T = r_U = r_K = r_M = 8 A (one point of the 6/8/10/12 A sweep,
+--radius selects another), K0 from a Chebyshev Fermi-operator expansion
+(order 200, kT = 0.01 Ha, untimed), x delta kick kappa = 1e-3, dt = 0.05 a.u.,
+exponential-midpoint propagator with 6 Taylor terms, U rebuilt every step.
+
+A step is one pass of the whole path: H(t+dt/2), T = S^-1 H, Taylor powers,
+U, the sandwich K <- U K U^dagger and the traces Tr(KS), Tr(KD_xyz).
+
+Two GPU paths are timed: the plain FP64 path and the mixed path (FP32 block
+products in the delta form K + dU K + K dU^dagger + dU K dU^dagger with K,
+its update sums and the traces in FP64).  `value` is the mixed path when its
+dipole agrees with the FP64 path to 1e-6 relative over the run, else FP64.
+
+--impl reference times the CPU oracle (plain C, all host cores) on a row
+sample of the same step and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--radius", type=float, default=8.0)
+    ap.add_argument("--ncell", type=int, default=8)
+    ap.add_argument("--basis", default="spd13")
+    ap.add_argument("--prop", default="em", choices=["em", "cn"])
+    ap.add_argument("--foe-order", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
+    return ap.parse_args()
+
+
+def workload(args):
+    import synth
+    s = synth.diamond_system(args.ncell, args.basis, 7.0, 7.0)
+    return s
+
+
+def model_spectrum(args):
+    """mu (mid-gap at valence filling) and spectral bounds from a 2x2x2 cell of
+    the same model (dense generalised diagonalisation; input preparation)."""
+    import synth
+    small = synth.diamond_system(2, args.basis, 7.0, 7.0)
+    _, w, _ = synth.ground_state_dense(small, 2 * small.n_atoms)
+    n_occ = 2 * small.n_atoms
+    mu = 0.5 * (w[n_occ - 1] + w[n_occ])
+    return mu, float(w.min()) - 0.5, float(w.max()) + 0.5
+
+
+def cfg_name(args):
+    return (f"diamond {args.ncell ** 3 * 8} atoms x {synth_nfunc(args.basis)} functions, r_S=r_H=7A, "
+            f"r_Sinv=r_T=r_U=r_K=r_M={args.radius:g}A, dt=0.05, {args.prop.upper()} 6 terms, x-kick 1e-3")
+
+
+def synth_nfunc(basis):
+    return {"sp4": 4, "spd13": 13, "h1": 1}[basis]
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# peaks
+# ----------------------------------------------------------------------------
+def measured_peaks():
+    p = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            p = json.load(open(path))
+        except Exception:
+            p = {}
+    return p
+
+
+def alu_peaks(torch):
+    """FP64 and FP32 (no TF32) GEMM throughput measured with cuBLAS through torch
+    (denominators for the ALU-bound block products), TFLOP/s."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n in [("fp64", torch.float64, 4096), ("fp32", torch.float32, 8192)]:
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            for _ in range(2):
+                torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = 1e9
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = 2.0 * n ** 3 / best / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    import paper_1404_5776_gb300 as rtm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    rtm.build()
+    dev_name = torch.cuda.get_device_name()
+
+    s = workload(args)
+    mu, e_lo, e_hi = model_spectrum(args)
+    R = args.radius
+    radii = dict(r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
+    common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=8192, **radii)
+
+    # --- FP64 context: ground state (untimed set-up), kick, FP64 steps
+    c64 = rtm.RT(s, precision="fp64", **common)
+    it64, res64 = c64.inverse()
+    c64.ground_state(0, args.foe_order, mu, 0.01, e_lo, e_hi)
+    c64.kick(0, 0, 0, 1e-3)
+    K1 = c64.matrix(0, rtm.RT_MAT_K)  # K(0+), kept to seed the mixed path
+    c32 = rtm.RT(s, precision="fp32", **common)
+    c32.inverse()
+    c32.set_density(0, 0, K1)
+
+    n64 = args.fp64_steps if args.fp64_steps is not None else args.steps
+    res = {}
+
+    def timed(ctx, nsteps, warm):
+        ctx.step(warm)
+        ctx.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        ctx.step(nsteps)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / max(nsteps, 1)
+
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_r{rank}.csv")
+    clocks.start()
+    ms64 = timed(c64, n64, args.warmup)
+    ms32 = timed(c32, args.steps, args.warmup)
+    clk = clocks.stop()
+
+    flops64, bytes64 = c64.step_work()
+    flops32, bytes32 = c32.step_work()
+
+    # dipole agreement over the steps both paths ran from the same K(0+)
+    o64 = c64.observables(0, 0)
+    o32 = c32.observables(0, 0)
+    m = min(len(o64), len(o32))
+    p64, p32 = o64[:m, 3], o32[:m, 3]
+    dip_rel = float(np.abs(p32 - p64).max() / np.abs(p64).max()) if m else float("nan")
+    ind = np.abs(p64 - p64[0]).max() if m else float("nan")
+    dip_rel_ind = float(np.abs(p32 - p64).max() / ind) if m and ind > 0 else float("nan")
+    trks_drift32 = float(np.abs(o32[:, 1] - o32[0, 1]).max() / abs(o32[0, 1])) if len(o32) else float("nan")
+
+    # per-kernel-class times (CUDA events on the library stream), a short extra pass
+    prof = {}
+    for name, ctx, n in (("fp64", c64, 2), ("fp32", c32, 5)):
+        ctx.profile(True)
+        ctx.step(n)
+        prof[name] = ctx.profile_read()
+        ctx.profile(False)
+
+    # e2e through the public API with host buffers: set K(0+) from host memory,
+    # run the steps, read the observables back
+    e2e = None
+    headline_ok = (dip_rel <= 1e-6)
+    ctx_e2e = c32 if headline_ok else c64
+    n_e2e = args.steps if headline_ok else n64
+    K1_host = np.ascontiguousarray(K1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    ctx_e2e.set_density(0, 0, K1_host)
+    ctx_e2e.step(n_e2e)
+    obs_e2e = ctx_e2e.observables(0, 0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = K1_host.nbytes / n_e2e
+    d2h = obs_e2e.nbytes / n_e2e
+
+    # roofline of the dominant kernel class of the headline path
+    hp = "fp32" if headline_ok else "fp64"
+    pr = prof[hp]
+    dom = max(pr, key=lambda k: pr[k]["ms"])
+    d = pr[dom]
+    per_launch_flops = d["flops"] / max(d["launches"], 1)
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    peaks = alu_peaks(torch) if rank == 0 else {}
+    mp = measured_peaks()
+    if d["flops"] > 0:
+        achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12
+        peak = peaks.get(hp)
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3) if peak else None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None, "traffic": None,
+                "peak_source": f"measured: cuBLAS {'SGEMM (TF32 off)' if hp == 'fp32' else 'DGEMM'} 2n^3/t on this GPU",
+                "per_launch_flops": per_launch_flops, "per_launch_ms": round(per_launch_ms, 4)}
+    else:
+        achieved = d["bytes"] / max(d["launches"], 1) / (per_launch_ms / 1e3) / 1e9
+        peak = mp.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None}
+
+    value_steps = 1e3 / (ms32 if headline_ok else ms64)
+    launches_per_step = (c32 if headline_ok else c64).step_kernels()
+    line = {
+        "metric": "TDDFT steps/sec & block GFLOP/s vs plain FP64 GPU path at dipole err<=1e-6",
+        "value": round(value_steps * world, 4),
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms32 if headline_ok else ms64, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if headline_ok else "f64",
+        "data": "synthetic (seeded diamond-lattice Gaussian model; no paper data)",
+        "config": {"workload": cfg_name(args), "n_atoms": s.n_atoms, "n": int(s.n), "radius_A": R,
+                   "l2": "inputs larger than L2 (K alone %.2f GB > 129 MB)" % (K1.nbytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "paths": {
+            "fp64": {"ms_per_step": round(ms64, 3), "steps_per_s": round(1e3 / ms64, 4),
+                     "gflops": round(flops64 / (ms64 / 1e3) / 1e9, 2), "timed_steps": n64},
+            "fp32_mixed": {"ms_per_step": round(ms32, 3), "steps_per_s": round(1e3 / ms32, 4),
+                           "gflops": round(flops32 / (ms32 / 1e3) / 1e9, 2), "timed_steps": args.steps},
+            "speedup_mixed_vs_fp64": round(ms64 / ms32, 2),
+            "algorithmic_flops_per_step": flops64,
+            "dipole_rel_err_mixed_vs_fp64": dip_rel,
+            "dipole_err_rel_to_induced": dip_rel_ind,
+            "trks_rel_drift_mixed": trks_drift32,
+            "compared_steps": int(m),
+            "hotelling": {"iters": it64, "residual": res64},
+        },
+        "roofline": roof,
+        "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                    for k, v in prof[hp].items() if v["launches"]},
+        "e2e": {"value": round(n_e2e / e2e_s * world, 4), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "what": "rt_set_density(K(0+) from host) + rt_step(n) + rt_observables, timed on the host"},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": clk,
+        "device": dev_name,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, s, budget_s=20.0)
+    c64.close()
+    c32.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+def oracle_step_sample(args, s, rows):
+    """Times the oracle's truncated products of one EM step for output block
+    rows [0, rows) and returns (seconds, rows).  Operand values do not change
+    the work of the plain C product, so S stands in for S^-1 on its pattern."""
+    import oracle
+    R = args.radius
+    pat = oracle.pattern(s.pos, s.cell, R)
+    S = oracle.BlockMatrix(s.bsize, oracle.Pattern(s.s_rowptr, s.s_col), s.s_val)
+    H = oracle.BlockMatrix(s.bsize, oracle.Pattern(s.h_rowptr, s.h_col), s.h_val)
+    Sinv = oracle.restrict(S, pat)
+    K = oracle.zeros(s.bsize, pat)
+    K.val[:] = 0.01 + 0.002j
+    t0 = time.perf_counter()
+    T = oracle.spgemm(Sinv, H, pat, rows=(0, rows))
+    P = T
+    for _ in range(2, 6):
+        P = oracle.spgemm(T, P, pat, rows=(0, rows))
+    U = P  # U = I + sum c_n T^n: an O(nnz) vector update, left out of the row sample
+    M = oracle.spgemm(U, K, pat, rows=(0, rows))
+    Kn = oracle.zeros(s.bsize, pat)
+    oracle.spgemm(M, U, pat, b_dag=True, upper_only=True, out=Kn, rows=(0, rows))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, s, budget_s=20.0):
+    import oracle
+    oracle.build()
+    # calibrate the row sample to about budget_s of CPU work
+    rows = 4
+    t = oracle_step_sample(args, s, rows)
+    rows = int(max(4, min(s.n_atoms, rows * budget_s / max(t, 1e-3))))
+    t = oracle_step_sample(args, s, rows)
+    step_s = t * s.n_atoms / rows
+    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": oracle.lib().or_num_threads(), "kind": "oracle",
+            "sample": f"oracle truncated products of one EM step (T, 4 Taylor powers, U K, M U^dagger) for "
+                      f"{rows} of {s.n_atoms} block rows ({t:.1f} s), extrapolated linearly to all rows"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    s = workload(args)
+    rows = 4
+    t = oracle_step_sample(args, s, rows)
+    rows = int(max(4, min(s.n_atoms, rows * 3.0 / max(t, 1e-3))))  # ~3 s per sampled step
+    for _ in range(args.warmup):
+        oracle_step_sample(args, s, rows)
+    tot = 0.0
+    for _ in range(args.steps):
+        tot += oracle_step_sample(args, s, rows)
+    step_s = (tot / max(args.steps, 1)) * s.n_atoms / rows
+    v = 1.0 / step_s
+    cores = oracle.lib().or_num_threads()
+    sample = (f"each step: oracle truncated products of one EM step for {rows} of {s.n_atoms} block rows, "
+              f"extrapolated linearly to all rows")
+    line = {"metric": "TDDFT steps/sec & block GFLOP/s vs plain FP64 GPU path at dipole err<=1e-6",
+            "value": v, "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded diamond-lattice Gaussian model)",
+            "config": {"workload": cfg_name(args), "n_atoms": s.n_atoms, "n": int(s.n), "radius_A": args.radius},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -224,6 +224,9 @@ RT_API rt_status rt_unitarity(rt_ctx* ctx, int32_t sys, int32_t metric_S, double
  * and written by those products once each. */
 RT_API rt_status rt_step_work(rt_ctx* ctx, double* flops, double* bytes);
 
+/* Number of kernels one step launches (the nodes of the captured step graph). */
+RT_API rt_status rt_step_kernels(rt_ctx* ctx, int64_t* kernels);
+
 /* Per-kernel-class timing: enable=1 makes later rt_step calls launch without
  * a graph and bracket each kernel with CUDA events on the context stream;
  * rt_profile_read returns, per class c < *n_classes (<= max), the launch

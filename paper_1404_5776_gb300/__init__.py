@@ -36,7 +36,7 @@ OBS_FIELDS = ["t", "trks_re", "trks_im", "trkdx_re", "trkdx_im", "trkdy_re", "tr
 
 EXPORTED = ["rt_default_params", "rt_create", "rt_set_field", "rt_inverse", "rt_set_density", "rt_ground_state",
             "rt_kick", "rt_propagator", "rt_step", "rt_observables", "rt_pattern_size", "rt_get_pattern",
-            "rt_matrix_size", "rt_get_matrix", "rt_unitarity", "rt_step_work", "rt_profile", "rt_profile_read",
+            "rt_matrix_size", "rt_get_matrix", "rt_unitarity", "rt_step_work", "rt_step_kernels", "rt_profile", "rt_profile_read",
             "rt_get_state", "rt_set_state", "rt_synchronize", "rt_last_error", "rt_destroy"]
 
 
@@ -100,6 +100,7 @@ def load(path: Optional[str] = None):
         "rt_get_matrix": [P, I32, I32, I32, P, I64],
         "rt_unitarity": [P, I32, I32, P, P],
         "rt_step_work": [P, P, P],
+        "rt_step_kernels": [P, P],
         "rt_profile": [P, I32],
         "rt_profile_read": [P, I32, P, P, P, P, P, P],
         "rt_get_state": [P, P, P],
@@ -327,6 +328,11 @@ class RT:
         f, b = ctypes.c_double(), ctypes.c_double()
         self._c(self.lib.rt_step_work(self.ctx, ctypes.byref(f), ctypes.byref(b)))
         return f.value, b.value
+
+    def step_kernels(self) -> int:
+        n = ctypes.c_int64()
+        self._c(self.lib.rt_step_kernels(self.ctx, ctypes.byref(n)))
+        return n.value
 
     def profile(self, enable: bool = True):
         self._c(self.lib.rt_profile(self.ctx, int(enable)))

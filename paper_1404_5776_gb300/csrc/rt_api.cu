@@ -111,6 +111,7 @@ struct rt_ctx {
   bool profiling = false;
   bool counting = false;
   double count_flops = 0.0, count_bytes = 0.0;
+  int64_t count_kernels = 0;
   struct Prof {
     int64_t launches = 0;
     double ms = 0, flops = 0, bytes = 0;
@@ -132,10 +133,11 @@ namespace rt {
 // helpers
 // ----------------------------------------------------------------------------
 template <class F>
-static void run(rt_ctx* c, int cls, double flops, double bytes, F&& f) {
+static void run(rt_ctx* c, int cls, double flops, double bytes, F&& f, int kernels = 1) {
   if (c->counting) {
     c->count_flops += flops;
     c->count_bytes += bytes;
+    c->count_kernels += kernels;
     return;
   }
   if (c->profiling) {
@@ -267,9 +269,9 @@ static GemmArgs args(const void* A, const void* B, void* C) {
 
 // residual ||I - Y||_F / sqrt(n) from the per-item partials of an EPI_TWO_I product
 static void residual_from_items(rt_ctx* c, Sys& s, const TripleInfo& ti, double* out, double* out2) {
-  run(c, PC_MISC, 0, 0, [&] {
-    launch_sum(s.red_items, ti.t.n_items, s.red_part, std::sqrt((double)s.n_true), out, out2, c->ws);
-  });
+  run(
+      c, PC_MISC, 0, 0,
+      [&] { launch_sum(s.red_items, ti.t.n_items, s.red_part, std::sqrt((double)s.n_true), out, out2, c->ws); }, 2);
 }
 
 // ----------------------------------------------------------------------------
@@ -539,11 +541,14 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
       prev = bufs[n % 2];
     }
   } else {
-    run(c, PC_TAYLOR, 0, 0, [&] {
-      launch_d2f(T, s.Tf, (int64_t)nvals(s, s.pT), c->ws);
-      launch_taylor_init(s.dUf, true, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
-                         terms > 1 ? c1 : 0.0, c1i, 0, c->ws);
-    });
+    run(
+        c, PC_TAYLOR, 0, 0,
+        [&] {
+          launch_d2f(T, s.Tf, (int64_t)nvals(s, s.pT), c->ws);
+          launch_taylor_init(s.dUf, true, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
+                             terms > 1 ? c1 : 0.0, c1i, 0, c->ws);
+        },
+        2);
     const float* prev = s.Tf;
     float* bufs[2] = {s.Pf0, s.Pf1};
     for (int n = 2; n < terms; ++n) {
@@ -643,11 +648,14 @@ static void sandwich(rt_ctx* c, Sys& s, int kick, int slot) {
 
 static void observe(rt_ctx* c, Sys& s, int kick, int slot) {
   double bytes = 16.0 * nvals(s, s.pK) + 8.0 * 4 * nvals(s, s.pH);
-  run(c, PC_OBS, 0, bytes, [&] {
-    launch_traces(s.K[kick], s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S, s.k_to_sT, s.D[0], s.D[1],
-                  s.D[2], s.k_to_hT, s.red_part, c->dstate, slot, c->ring, c->p.obs_capacity, c->n_slots, slot,
-                  c->ws);
-  });
+  run(
+      c, PC_OBS, 0, bytes,
+      [&] {
+        launch_traces(s.K[kick], s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S, s.k_to_sT, s.D[0], s.D[1],
+                      s.D[2], s.k_to_hT, s.red_part, c->dstate, slot, c->ring, c->p.obs_capacity, c->n_slots, slot,
+                      c->ws);
+      },
+      2);
 }
 
 static void enqueue_step(rt_ctx* c) {
@@ -1237,6 +1245,24 @@ rt_status rt_step_work(rt_ctx* c, double* flops, double* bytes) {
     c->counting = false;
     *flops = c->count_flops;
     *bytes = c->count_bytes;
+    return RT_OK;
+  });
+}
+
+rt_status rt_step_kernels(rt_ctx* c, int64_t* kernels) {
+  return guarded(c, [&] {
+    RT_REQUIRE(kernels, RT_EINVAL, "NULL output");
+    c->counting = true;
+    c->count_flops = c->count_bytes = 0.0;
+    c->count_kernels = 0;
+    try {
+      enqueue_step(c);
+    } catch (...) {
+      c->counting = false;
+      throw;
+    }
+    c->counting = false;
+    *kernels = c->count_kernels;
     return RT_OK;
   });
 }
