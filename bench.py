@@ -245,6 +245,8 @@ def run_gpu(args):
     ind = np.abs(p64 - p64[0]).max() if m else float("nan")
     dip_rel_ind = float(np.abs(p32 - p64).max() / ind) if m and ind > 0 else float("nan")
     trks_drift32 = float(np.abs(o32[:, 1] - o32[0, 1]).max() / abs(o32[0, 1])) if len(o32) else float("nan")
+    trks_drift64 = float(np.abs(o64[:, 1] - o64[0, 1]).max() / abs(o64[0, 1])) if len(o64) else float("nan")
+    trks_diff = float(np.abs(o32[:m, 1] - o64[:m, 1]).max() / abs(o64[0, 1])) if m else float("nan")
 
     # per-kernel-class times (CUDA events on the library stream), a short extra pass
     prof = {}
@@ -292,6 +294,7 @@ def run_gpu(args):
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3) if peak else None,
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None, "traffic": None,
                 "peak_source": f"measured: cuBLAS {'SGEMM (TF32 off)' if hp == 'fp32' else 'DGEMM'} 2n^3/t on this GPU",
+                "measured_peaks_tflops": {k: round(v, 3) for k, v in peaks.items()},
                 "per_launch_flops": per_launch_flops, "per_launch_ms": round(per_launch_ms, 4)}
     else:
         achieved = d["bytes"] / max(d["launches"], 1) / (per_launch_ms / 1e3) / 1e9
@@ -327,6 +330,8 @@ def run_gpu(args):
             "dipole_rel_err_mixed_vs_fp64": dip_rel,
             "dipole_err_rel_to_induced": dip_rel_ind,
             "trks_rel_drift_mixed": trks_drift32,
+            "trks_rel_drift_fp64": trks_drift64,
+            "trks_rel_diff_mixed_vs_fp64": trks_diff,
             "compared_steps": int(m),
             "hotelling": {"iters": it64, "residual": res64},
         },

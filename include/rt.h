@@ -215,7 +215,9 @@ RT_API rt_status rt_get_matrix(rt_ctx* ctx, int32_t sys, int32_t kick, int32_t w
 /* Unitarity of the last propagator of `sys` (paper Sec. IV, eq. s_unit):
  * with metric_S = 1, E = cut_{P_U}(U^dagger cut_{P_W}(S U)) - S (the conserved
  * form in a non-orthogonal basis); with 0, E = cut_{P_U}(U^dagger U) - I (the
- * printed form).  Host outputs max|E| and mean|E| over the entries of P_U. */
+ * printed form).  Host outputs max|E| and mean|E| over the entries of P_U.
+ * In the FP32 EM mode the propagator is held as U - I in FP32; it is promoted
+ * to U = I + (U - I) in FP64 first, so E measures the mixed propagator. */
 RT_API rt_status rt_unitarity(rt_ctx* ctx, int32_t sys, int32_t metric_S, double* maxabs, double* meanabs);
 
 /* Algorithmic work of one step summed over systems and kicks:

@@ -64,7 +64,8 @@ void launch_field_axpy(const double* H0, const double* D, const DevState* s, dou
 template <typename CV, typename RV>
 __global__ void k_taylor_init(CV* __restrict__ U, int64_t nnzb_u, const int32_t* __restrict__ u_rowidx,
                               const int32_t* __restrict__ u_col, const RV* __restrict__ T,
-                              const int32_t* __restrict__ u_to_t, int B, double c1, int c1_imag, int ident) {
+                              const int32_t* __restrict__ u_to_t, int B, int urs, double c1, int c1_imag,
+                              int ident) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t NE = (int64_t)B * B;
   for (; idx < nnzb_u * NE; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -82,10 +83,12 @@ __global__ void k_taylor_init(CV* __restrict__ U, int64_t nnzb_u, const int32_t*
     CV v;
     v.x = (decltype(v.x))re;
     v.y = (decltype(v.y))im;
-    U[idx] = v;
+    U[q * (int64_t)B * urs + r * urs + c] = v;
   }
 }
 
+// U (FP64, dense blocks) = ident*I + c1 T, or the FP32 difference dU = c1 T
+// in the FP32 block layout (row stride rs32(B)); T is FP64 with dense blocks.
 void launch_taylor_init(void* U, bool fp32, int64_t nnzb_u, const int32_t* u_rowidx, const int32_t* u_col,
                         const void* T, bool t_fp32, const int32_t* u_to_t, int B, double c1, int c1_imag, int ident,
                         cudaStream_t st) {
@@ -93,17 +96,14 @@ void launch_taylor_init(void* U, bool fp32, int64_t nnzb_u, const int32_t* u_row
   if (n == 0) return;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  if (!fp32 && !t_fp32)
+  if (t_fp32) throw Error{RT_EINTERNAL, "taylor init takes an FP64 T"};
+  if (!fp32)
     k_taylor_init<double2, double><<<(unsigned)g, 256, 0, st>>>((double2*)U, nnzb_u, u_rowidx, u_col,
-                                                                (const double*)T, u_to_t, B, c1, c1_imag, ident);
-  else if (fp32 && !t_fp32)
-    k_taylor_init<float2, double><<<(unsigned)g, 256, 0, st>>>((float2*)U, nnzb_u, u_rowidx, u_col,
-                                                               (const double*)T, u_to_t, B, c1, c1_imag, ident);
-  else if (fp32 && t_fp32)
-    k_taylor_init<float2, float><<<(unsigned)g, 256, 0, st>>>((float2*)U, nnzb_u, u_rowidx, u_col,
-                                                              (const float*)T, u_to_t, B, c1, c1_imag, ident);
+                                                                (const double*)T, u_to_t, B, B, c1, c1_imag, ident);
   else
-    throw Error{RT_EINTERNAL, "taylor init variant"};
+    k_taylor_init<float2, double><<<(unsigned)g, 256, 0, st>>>((float2*)U, nnzb_u, u_rowidx, u_col,
+                                                               (const double*)T, u_to_t, B, rs32(B), c1, c1_imag,
+                                                               ident);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -255,51 +255,58 @@ void launch_sum(const double* v, int64_t n, double* part, double sqrt_div, doubl
 
 // Tr(K X) terms: for each block (i,j) of P_K, sum_ab K_ij[a,b] X_ji[b,a] over
 // the true functions; X gathered through kx_map (block (j,i) of X, or -1).
-// Four traces at once: X in {S, Dx, Dy, Dz}; results complex.
+// Four traces at once: X in {S, Dx, Dy, Dz}; results complex.  One warp per
+// block (coalesced reads of K), fixed block-to-warp assignment, fixed-order
+// reductions: the result does not depend on scheduling.
 __global__ void k_traces(const double2* __restrict__ K, int64_t nnzb, const int32_t* __restrict__ rowidx,
                          const int32_t* __restrict__ col, const int32_t* __restrict__ bsize, int B,
                          const double* __restrict__ S, const int32_t* __restrict__ ks_map,
                          const double* __restrict__ Dx, const double* __restrict__ Dy, const double* __restrict__ Dz,
                          const int32_t* __restrict__ kd_map, double* __restrict__ part) {
-  __shared__ double s[8][RED_T];
+  __shared__ double s[8][RED_T / 32];
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   const int NE = B * B;
-  for (int64_t q = (int64_t)blockIdx.x * RED_T + threadIdx.x; q < nnzb; q += (int64_t)gridDim.x * RED_T) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (RED_T / 32) + warp;
+  const int64_t nw = (int64_t)gridDim.x * (RED_T / 32);
+  for (int64_t q = gw; q < nnzb; q += nw) {
     int i = rowidx[q], j = col[q];
     int bi = bsize[i], bj = bsize[j];
     int sq = ks_map[q], dq = kd_map[q];
     const double2* k = K + q * NE;
-    for (int a = 0; a < bi; ++a)
-      for (int b = 0; b < bj; ++b) {
-        double2 kv = k[a * B + b];
-        int te = b * B + a;  // X_ji[b][a]
-        if (sq >= 0) {
-          double x = S[(int64_t)sq * NE + te];
-          acc[0] += kv.x * x;
-          acc[1] += kv.y * x;
-        }
-        if (dq >= 0) {
-          double x = Dx[(int64_t)dq * NE + te];
-          acc[2] += kv.x * x;
-          acc[3] += kv.y * x;
-          x = Dy[(int64_t)dq * NE + te];
-          acc[4] += kv.x * x;
-          acc[5] += kv.y * x;
-          x = Dz[(int64_t)dq * NE + te];
-          acc[6] += kv.x * x;
-          acc[7] += kv.y * x;
-        }
+    for (int e = lane; e < bi * bj; e += 32) {
+      int a = e / bj, b = e - a * bj;
+      double2 kv = k[a * B + b];
+      int te = b * B + a;  // X_ji[b][a]
+      if (sq >= 0) {
+        double x = S[(int64_t)sq * NE + te];
+        acc[0] += kv.x * x;
+        acc[1] += kv.y * x;
       }
+      if (dq >= 0) {
+        double x = Dx[(int64_t)dq * NE + te];
+        acc[2] += kv.x * x;
+        acc[3] += kv.y * x;
+        x = Dy[(int64_t)dq * NE + te];
+        acc[4] += kv.x * x;
+        acc[5] += kv.y * x;
+        x = Dz[(int64_t)dq * NE + te];
+        acc[6] += kv.x * x;
+        acc[7] += kv.y * x;
+      }
+    }
   }
-  for (int c = 0; c < 8; ++c) s[c][threadIdx.x] = acc[c];
+  for (int c = 0; c < 8; ++c)
+    for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], off);
+  if (lane == 0)
+    for (int c = 0; c < 8; ++c) s[c][warp] = acc[c];
   __syncthreads();
-  for (int off = RED_T / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off)
-      for (int c = 0; c < 8; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + off];
-    __syncthreads();
-  }
   if (threadIdx.x == 0)
-    for (int c = 0; c < 8; ++c) part[blockIdx.x * 8 + c] = s[c][0];
+    for (int c = 0; c < 8; ++c) {
+      double t = 0.0;
+      for (int w = 0; w < RED_T / 32; ++w) t += s[c][w];
+      part[blockIdx.x * 8 + c] = t;
+    }
 }
 
 // Sums the trace partials in fixed order and writes one observables record.
@@ -507,34 +514,70 @@ void launch_symmetrise_to_complex(const double* Kr, double2* K, int64_t nnzb, co
 // ---------------------------------------------------------------------------
 // precision conversions and the delta-form operand W = K + M (FP32)
 // ---------------------------------------------------------------------------
-__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
+// FP64 dense blocks -> FP32 blocks with row stride rs (ncomp = 1 real, 2 complex)
+__global__ void k_d2f_pad(const double* __restrict__ a, float* __restrict__ b, int64_t nnzb, int B, int rs,
+                          int ncomp) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    int64_t o = q * (int64_t)B * rs + r * rs + c;
+    for (int k = 0; k < ncomp; ++k) b[ncomp * o + k] = (float)a[ncomp * idx + k];
+  }
 }
 
-void launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st) {
+void launch_d2f_pad(const double* a, float* b, int64_t nnzb, int B, bool cplx, cudaStream_t st) {
+  int64_t n = nnzb * B * B;
   if (n == 0) return;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  k_d2f<<<(unsigned)g, 256, 0, st>>>(a, b, n);
+  k_d2f_pad<<<(unsigned)g, 256, 0, st>>>(a, b, nnzb, B, rs32(B), cplx ? 2 : 1);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
-// W[q] = (float)K[mk[q]] + M[q] on P_M (complex)
-__global__ void k_delta_w(const double2* __restrict__ K, const int32_t* __restrict__ m_to_k,
-                          const float2* __restrict__ Mf, float2* __restrict__ Wf, int64_t nnzb_m, int NE) {
+// dUH[q] = conj(dU[q])^T (FP32 complex, same block index, FP32 block layout)
+__global__ void k_dagger32(const float2* __restrict__ dU, float2* __restrict__ dUH, int64_t nnzb, int B, int rs) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    float2 v = dU[q * (int64_t)B * rs + c * rs + r];
+    dUH[q * (int64_t)B * rs + r * rs + c] = make_float2(v.x, -v.y);
+  }
+}
+
+void launch_dagger32(const float2* dU, float2* dUH, int64_t nnzb, int B, cudaStream_t st) {
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_dagger32<<<(unsigned)g, 256, 0, st>>>(dU, dUH, nnzb, B, rs32(B));
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// W[q] = (float)K[mk[q]] + M[q] on P_M (complex; K dense FP64 blocks, M and
+// W in the FP32 block layout)
+__global__ void k_delta_w(const double2* __restrict__ K, const int32_t* __restrict__ m_to_k,
+                          const float2* __restrict__ Mf, float2* __restrict__ Wf, int64_t nnzb_m, int B, int rs) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
   for (; idx < nnzb_m * NE; idx += (int64_t)gridDim.x * blockDim.x) {
     int64_t q = idx / NE;
     int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    int64_t o = q * (int64_t)B * rs + r * rs + c;
     int kq = m_to_k ? m_to_k[q] : (int)q;
-    float2 m = Mf[idx];
+    float2 m = Mf[o];
     if (kq >= 0) {
       double2 k = K[(int64_t)kq * NE + e];
       m.x = (float)((double)m.x + k.x);
       m.y = (float)((double)m.y + k.y);
     }
-    Wf[idx] = m;
+    Wf[o] = m;
   }
 }
 
@@ -544,7 +587,7 @@ void launch_delta_w(const double2* K, const int32_t* m_to_k, const float2* Mf, f
   if (n == 0) return;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  k_delta_w<<<(unsigned)g, 256, 0, st>>>(K, m_to_k, Mf, Wf, nnzb_m, B * B);
+  k_delta_w<<<(unsigned)g, 256, 0, st>>>(K, m_to_k, Mf, Wf, nnzb_m, B, rs32(B));
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -560,7 +603,7 @@ void launch_set_hot(DevState* s, const double* resid, int iters, cudaStream_t st
 
 // dU = U - I in FP32 (CN delta form)
 __global__ void k_u_minus_i_f32(const double2* __restrict__ U, float2* __restrict__ dU, int64_t nnzb,
-                                const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B) {
+                                const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B, int rs) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t NE = (int64_t)B * B;
   for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -569,7 +612,7 @@ __global__ void k_u_minus_i_f32(const double2* __restrict__ U, float2* __restric
     int r = e / B, c = e - r * B;
     double2 u = U[idx];
     double d = (rowidx[q] == col[q] && r == c) ? 1.0 : 0.0;
-    dU[idx] = make_float2((float)(u.x - d), (float)u.y);
+    dU[q * (int64_t)B * rs + r * rs + c] = make_float2((float)(u.x - d), (float)u.y);
   }
 }
 
@@ -579,7 +622,32 @@ void launch_u_minus_i_f32(const double2* U, float2* dU, int64_t nnzb, const int3
   if (n == 0) return;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  k_u_minus_i_f32<<<(unsigned)g, 256, 0, st>>>(U, dU, nnzb, rowidx, col, B);
+  k_u_minus_i_f32<<<(unsigned)g, 256, 0, st>>>(U, dU, nnzb, rowidx, col, B, rs32(B));
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// U = I + dU (FP32 difference promoted to FP64), for diagnostics of the mixed path
+__global__ void k_u_from_delta(const float2* __restrict__ dU, double2* __restrict__ U, int64_t nnzb,
+                               const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B, int rs) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    float2 d = dU[q * (int64_t)B * rs + r * rs + c];
+    double one = (rowidx[q] == col[q] && r == c) ? 1.0 : 0.0;
+    U[idx] = make_double2(one + (double)d.x, (double)d.y);
+  }
+}
+
+void launch_u_from_delta(const float2* dU, double2* U, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B,
+                         cudaStream_t st) {
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_u_from_delta<<<(unsigned)g, 256, 0, st>>>(dU, U, nnzb, rowidx, col, B, rs32(B));
   RT_CUDA_CHECK(cudaGetLastError());
 }
 

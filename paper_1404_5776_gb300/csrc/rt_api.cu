@@ -70,7 +70,7 @@ struct Sys {
   double2 *Sc = nullptr, *W = nullptr, *E = nullptr;
   // FP32 buffers (mixed precision)
   float *Tf = nullptr, *Pf0 = nullptr, *Pf1 = nullptr;
-  float2 *dUf = nullptr, *Kf = nullptr, *Mf = nullptr, *Wf = nullptr;
+  float2 *dUf = nullptr, *dUH = nullptr, *Kf = nullptr, *Mf = nullptr, *Wf = nullptr;
   // maps
   int32_t *u_to_t = nullptr, *a_to_s = nullptr, *a_to_h = nullptr, *k_to_sT = nullptr, *k_to_hT = nullptr;
   int32_t *u_to_sinv = nullptr, *k_to_sinv = nullptr, *u_to_s = nullptr, *k_to_m = nullptr, *m_to_k = nullptr;
@@ -99,6 +99,8 @@ struct rt_ctx {
   std::vector<std::unique_ptr<rt::Sys>> sys;
   rt::FieldParams field;
   rt::DevState* dstate = nullptr;
+  void* zero32 = nullptr;  // one zero FP32 complex block (padded layout)
+  int* d_err = nullptr;    // device error word of bounded waits
   double* ring = nullptr;  // [capacity][n_slots][RT_NOBS]
   int n_slots = 0;
   int64_t host_step = 0;  // steps enqueued since the last time reset
@@ -224,6 +226,8 @@ static TripleInfo& triples_for(rt_ctx* c, Sys& s, Pattern* A, bool ad, Pattern* 
 }
 
 static size_t nvals(const Sys& s, const Pattern* P) { return (size_t)P->nnzb * s.B * s.B; }
+// elements of an FP32 matrix (13-function blocks padded to 13 x 16)
+static size_t nvals32(const Sys& s, const Pattern* P) { return (size_t)P->nnzb * sb32(s.B); }
 
 static int32_t* block_map(rt_ctx* c, const Pattern* src, const Pattern* dst, bool transpose) {
   int32_t* m = c->arena.get_n<int32_t>(src->nnzb);
@@ -253,6 +257,8 @@ static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cpl
     g.tmap = C->tmap;
   }
   g.bsize = s.d_bsize;
+  g.zero = c->zero32;
+  g.err = c->d_err;
   int B = s.B;
   run(c, cls, gemm_flops(ti, cplx), gemm_bytes(s, ti, cplx, fp32),
       [&] { launch_gemm(B, fp32, cplx, ad, bd, epi, g, c->ws); });
@@ -420,14 +426,24 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
   }
   if (p.precision == RT_FP32) {
     RT_REQUIRE(p.r_M >= p.r_K, RT_EINVAL, "the FP32 delta-form sandwich needs r_M >= r_K");
-    s.dUf = c->arena.get_n<float2>(nvals(s, s.pU));
-    s.Kf = c->arena.get_n<float2>(nvals(s, s.pK));
-    s.Mf = c->arena.get_n<float2>(nvals(s, s.pM));
-    s.Wf = c->arena.get_n<float2>(nvals(s, s.pM));
+    s.dUf = c->arena.get_n<float2>(nvals32(s, s.pU));
+    if (s.B == 13) s.dUH = c->arena.get_n<float2>(nvals32(s, s.pU));
+    s.Kf = c->arena.get_n<float2>(nvals32(s, s.pK));
+    s.Mf = c->arena.get_n<float2>(nvals32(s, s.pM));
+    s.Wf = c->arena.get_n<float2>(nvals32(s, s.pM));
+    // the padding columns of 13-function FP32 blocks are never written: zero them once
+    RT_CUDA_CHECK(cudaMemsetAsync(s.dUf, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+    if (s.dUH) RT_CUDA_CHECK(cudaMemsetAsync(s.dUH, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+    RT_CUDA_CHECK(cudaMemsetAsync(s.Kf, 0, sizeof(float2) * nvals32(s, s.pK), c->ws));
+    RT_CUDA_CHECK(cudaMemsetAsync(s.Mf, 0, sizeof(float2) * nvals32(s, s.pM), c->ws));
+    RT_CUDA_CHECK(cudaMemsetAsync(s.Wf, 0, sizeof(float2) * nvals32(s, s.pM), c->ws));
     if (p.prop == RT_PROP_EM) {
-      s.Tf = c->arena.get_n<float>(nvals(s, s.pT));
-      s.Pf0 = c->arena.get_n<float>(nvals(s, s.pU));
-      s.Pf1 = c->arena.get_n<float>(nvals(s, s.pU));
+      s.Tf = c->arena.get_n<float>(nvals32(s, s.pT));
+      s.Pf0 = c->arena.get_n<float>(nvals32(s, s.pU));
+      s.Pf1 = c->arena.get_n<float>(nvals32(s, s.pU));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Tf, 0, sizeof(float) * nvals32(s, s.pT), c->ws));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Pf0, 0, sizeof(float) * nvals32(s, s.pU), c->ws));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Pf1, 0, sizeof(float) * nvals32(s, s.pU), c->ws));
       s.T0 = c->arena.get_n<double>(nvals(s, s.pT));
       s.TD = c->arena.get_n<double>(nvals(s, s.pT));
     }
@@ -523,7 +539,7 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
   int c1i = 0;
   taylor_coef(1, dt, &c1, &c1i);
   if (!fp32_delta) {
-    run(c, PC_TAYLOR, 0, 0, [&] {
+    run(c, PC_MISC, 0, 0, [&] {
       launch_taylor_init(s.U, false, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
                          terms > 1 ? c1 : 0.0, c1i, 1, c->ws);
     });
@@ -542,9 +558,9 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
     }
   } else {
     run(
-        c, PC_TAYLOR, 0, 0,
+        c, PC_MISC, 0, 0,
         [&] {
-          launch_d2f(T, s.Tf, (int64_t)nvals(s, s.pT), c->ws);
+          launch_d2f_pad(T, s.Tf, s.pT->nnzb, s.B, false, c->ws);
           launch_taylor_init(s.dUf, true, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
                              terms > 1 ? c1 : 0.0, c1i, 0, c->ws);
         },
@@ -555,13 +571,15 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
       double cn;
       int ci;
       taylor_coef(n, dt, &cn, &ci);
-      GemmArgs g = args(s.Tf, prev, bufs[n % 2]);
+      // the last power is needed only inside U: no store of C
+      GemmArgs g = args(s.Tf, prev, n == terms - 1 ? nullptr : bufs[n % 2]);
       g.U = s.dUf;
       g.coef = cn;
       g.coef_imag = ci;
       gemm(c, s, PC_TAYLOR, n == 2 ? t2 : tn, true, false, false, false, EPI_STORE_ACC, g, s.pU);
       prev = bufs[n % 2];
     }
+    if (s.dUH) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
   }
 }
 
@@ -613,6 +631,7 @@ static void build_propagator(rt_ctx* c, Sys& s) {
       // dU = U - I in FP32 for the delta-form sandwich
       run(c, PC_MISC, 0, 0,
           [&] { launch_u_minus_i_f32(s.U, s.dUf, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws); });
+      if (s.dUH) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
     }
   }
 }
@@ -634,15 +653,18 @@ static void sandwich(rt_ctx* c, Sys& s, int kick, int slot) {
     gemm(c, s, PC_MUDAG, tK, false, true, false, true, EPI_SANDWICH, g, s.pK);
   } else {
     // delta form: M = dU K, W = K + M, K' = K + M + W dU^dagger (K, sums in FP64)
-    run(c, PC_MISC, 0, 0, [&] { launch_d2f((const double*)K, (float*)s.Kf, 2 * (int64_t)nvals(s, s.pK), c->ws); });
+    run(c, PC_MISC, 0, 0, [&] { launch_d2f_pad((const double*)K, (float*)s.Kf, s.pK->nnzb, s.B, true, c->ws); });
     gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUf, s.Kf, s.Mf), s.pM);
     run(c, PC_MISC, 0, 0, [&] { launch_delta_w(K, s.m_to_k, s.Mf, s.Wf, s.pM->nnzb, s.B, c->ws); });
-    GemmArgs g = args(s.Wf, s.dUf, K);
+    // 13-function blocks read a pre-transposed (U - I)^dagger; the generic
+    // kernel transposes while staging
+    const bool pre_t = s.dUH != nullptr;
+    GemmArgs g = args(s.Wf, pre_t ? s.dUH : s.dUf, K);
     g.herm_max = herm;
     g.base = K;
     g.addend = s.Mf;
     g.add_map = s.k_to_m;
-    gemm(c, s, PC_MUDAG, tK, true, true, false, true, EPI_DELTA_SANDWICH, g, s.pK);
+    gemm(c, s, PC_MUDAG, tK, true, true, false, !pre_t, EPI_DELTA_SANDWICH, g, s.pK);
   }
 }
 
@@ -762,6 +784,8 @@ static void ensure_unitarity_lists(rt_ctx* c, Sys& s) {
 
 static void unitarity(rt_ctx* c, Sys& s, int metric, double* mx, double* mean) {
   ensure_unitarity_lists(c, s);
+  if (c->p.precision == RT_FP32 && c->p.prop == RT_PROP_EM)
+    launch_u_from_delta(s.dUf, s.U, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);  // U = I + dU
   if (metric) {
     TripleInfo& tW = triples_for(c, s, s.pS, false, s.pU, false, s.pW, false);
     TripleInfo& tE = triples_for(c, s, s.pU, true, s.pW, false, s.pU, false);
@@ -866,6 +890,14 @@ static rt_status guarded(rt_ctx* c, F&& f) {
   }
 }
 
+// Raises RT_ETIMEOUT when a kernel recorded that a bounded wait gave up.
+static void check_device_error(rt_ctx* c) {
+  int e = 0;
+  RT_CUDA_CHECK(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->ws));
+  RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+  if (e) throw Error{RT_ETIMEOUT, "a device-side bounded wait gave up (error word " + std::to_string(e) + ")"};
+}
+
 static rt_status check_sys(rt_ctx* c, int32_t sys) {
   if (sys < 0 || sys >= (int32_t)c->sys.size()) throw Error{RT_EINVAL, "system index out of range"};
   return RT_OK;
@@ -924,6 +956,10 @@ rt_status rt_create(rt_ctx** out, const rt_system* sys, int32_t n_sys, const rt_
     c->n_slots = n_sys * q.n_kick;
     c->read_upto.assign(c->n_slots, 0);
     c->dstate = c->arena.get_n<DevState>(1);
+    c->zero32 = c->arena.get(13 * 16 * sizeof(float2));
+    RT_CUDA_CHECK(cudaMemsetAsync(c->zero32, 0, 13 * 16 * sizeof(float2), c->ws));
+    c->d_err = c->arena.get_n<int>(1);
+    RT_CUDA_CHECK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->ws));
     c->ring = c->arena.get_n<double>((size_t)q.obs_capacity * c->n_slots * RT_NOBS);
     RT_CUDA_CHECK(cudaMemsetAsync(c->ring, 0, sizeof(double) * (size_t)q.obs_capacity * c->n_slots * RT_NOBS, c->ws));
     reset_time(c);
@@ -1128,6 +1164,7 @@ rt_status rt_observables(rt_ctx* c, int32_t sys, int32_t kick, double* out, int3
     std::vector<double> ring((size_t)cap * c->n_slots * RT_NOBS);
     RT_CUDA_CHECK(cudaMemcpyAsync(ring.data(), c->ring, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost, c->ws));
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    check_device_error(c);
     bool bad = false;
     for (int64_t k = 0; k < cnt; ++k) {
       int64_t r = (first + k) % cap;
@@ -1224,8 +1261,6 @@ rt_status rt_unitarity(rt_ctx* c, int32_t sys, int32_t metric_S, double* maxabs,
     check_sys(c, sys);
     RT_REQUIRE(maxabs && meanabs, RT_EINVAL, "NULL output");
     Sys& s = *c->sys[sys];
-    RT_REQUIRE(c->p.precision == RT_FP64 || s.u_ready || c->p.prop == RT_PROP_CN, RT_ESTATE,
-               "no FP64 propagator held (FP32 EM keeps U - I in FP32)");
     unitarity(c, s, metric_S ? 1 : 0, maxabs, meanabs);
     return RT_OK;
   });
@@ -1379,8 +1414,10 @@ rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
         RT_CUDA_CHECK(cudaMemcpyAsync(s.X, o, nu, cudaMemcpyHostToDevice, c->ws));
         o += nu;
       }
-      if (c->p.precision == RT_FP32 && s.dUf)
+      if (c->p.precision == RT_FP32 && s.dUf) {
         launch_u_minus_i_f32(s.U, s.dUf, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
+        if (s.dUH) launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws);
+      }
     }
     c->host_step = h.host_step;
     c->t_host = h.t_host;
@@ -1392,6 +1429,7 @@ rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
 rt_status rt_synchronize(rt_ctx* c) {
   return guarded(c, [&] {
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    check_device_error(c);
     return RT_OK;
   });
 }

@@ -55,10 +55,13 @@ void launch_scale(double* v, double c, int64_t n, cudaStream_t st);
 void launch_symmetrise_to_complex(const double* Kr, double2* K, int64_t nnzb, const int32_t* rowidx,
                                   const int32_t* col, const int32_t* tmap, const int32_t* bsize, int B,
                                   cudaStream_t st);
-void launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st);
+void launch_d2f_pad(const double* a, float* b, int64_t nnzb, int B, bool cplx, cudaStream_t st);
+void launch_dagger32(const float2* dU, float2* dUH, int64_t nnzb, int B, cudaStream_t st);
 void launch_delta_w(const double2* K, const int32_t* m_to_k, const float2* Mf, float2* Wf, int64_t nnzb_m, int B,
                     cudaStream_t st);
 void launch_set_hot(DevState* s, const double* resid, int iters, cudaStream_t st);
+void launch_u_from_delta(const float2* dU, double2* U, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B,
+                         cudaStream_t st);
 void launch_u_minus_i_f32(const double2* U, float2* dU, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
                           int B, cudaStream_t st);
 

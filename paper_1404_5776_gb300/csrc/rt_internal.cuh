@@ -147,7 +147,14 @@ struct GemmArgs {
   const void* addend;
   const int32_t* add_map;   // P_K block -> addend block
   unsigned long long* herm_max;  // max |K_ii - K_ii^dagger| bits
+  const void* zero;         // a zero block (FP32 kernels stage it for missing triples)
+  int* err;                 // device error word (bounded waits that gave up)
 };
+
+// Row stride of an FP32 block: 13-function blocks are padded to 13 x 16
+// (16-byte aligned rows, the shared-memory layout of the FP32 kernels).
+inline int rs32(int B) { return B == 13 ? 16 : B; }
+inline int sb32(int B) { return B * rs32(B); }
 
 // Launches; `cplx` selects complex values, `b_dag` conj-transposes B's blocks,
 // `a_dag` A's blocks.  Element type by precision: FP64 double/double2, FP32 float/float2.

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(GEMM_WARPS * 32) k_gemm(GemmArgs g) {
     for (int s = 0; s < EPL; ++s) {
       int e = gl + s * LPB;
       if (e < NE) {
-        C[(int64_t)q * NE + e] = acc[s];
+        if (C) C[(int64_t)q * NE + e] = acc[s];  // null: power needed only inside U
         if (uq >= 0) {
           CV u = U[(int64_t)uq * NE + e];
           if (g.coef_imag) u.y += (decltype(u.y))(g.coef * re_of(acc[s]));
@@ -351,8 +351,15 @@ static void dispatch_prec(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const
   throw Error{RT_EINTERNAL, "unsupported product variant"};
 }
 
+bool launch_gemm13_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const GemmArgs& g, cudaStream_t st);
+
 void launch_gemm(int B, bool fp32, bool cplx, bool a_dag, bool b_dag, Epilogue epi, const GemmArgs& g,
                  cudaStream_t st) {
+  if (B == 13 && fp32) {
+    // FP32 13-function matrices use the padded block layout of these kernels only
+    if (launch_gemm13_f32(cplx, a_dag, b_dag, epi, g, st)) return;
+    throw Error{RT_EINTERNAL, "FP32 13-function product variant has no kernel"};
+  }
   switch (B) {
     case 1: return fp32 ? dispatch_prec<1, float>(cplx, a_dag, b_dag, epi, g, st)
                         : dispatch_prec<1, double>(cplx, a_dag, b_dag, epi, g, st);

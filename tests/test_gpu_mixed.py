@@ -1,0 +1,76 @@
+"""Mixed-precision mode (FP32 block products, FP64 K and reductions) against
+the FP64 oracle.
+
+Bars (the accuracy targets of the mixed path): dipole Tr(K D_x) within 1e-6
+relative to |P| of the FP64 result, and the S-unitarity error of the mixed
+propagator exceeding the FP64 propagator's by at most 1e-8.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1404_5776_gb300 as m
+    m.build()
+    return m
+
+
+def _radii(r):
+    return dict(r_Sinv=r, r_T=r, r_U=r, r_K=r, r_M=r)
+
+
+def _pair(rt, basis, prop, steps, r=6.0):
+    s = synth.diamond_system(2, basis, 6.0, 6.0)
+    K0, _, _ = synth.ground_state_dense(s, 2 * s.n_atoms)
+    ctx = rt.RT(s, prop=prop, precision="fp32", **_radii(r))
+    ctx.inverse()
+    ctx.set_density_dense(0, 0, K0)
+    ctx.kick(0, 0, 0, 1e-3)
+    ctx.step(steps)
+    obs = ctx.observables(0, 0)
+    Kg = ctx.matrix(0, rt.RT_MAT_K)
+    ref = oracle.Propagator(s, oracle.Params(prop=prop, **_radii(r)))
+    ref.set_density_dense(K0)
+    ref.kick(0, 1e-3)
+    rows = []
+    for _ in range(steps):
+        out = ref.step()
+        rows.append([z for z in out["obs"]])
+    return ctx, obs, Kg, np.array(rows), ref
+
+
+@pytest.mark.parametrize("basis", ["spd13", "sp4"])
+@pytest.mark.parametrize("prop", ["em", "cn"])
+def test_mixed_dipole_and_density(rt, basis, prop):
+    ctx, obs, Kg, rows, ref = _pair(rt, basis, prop, 40)
+    ctx.close()
+    p64 = rows[:, 1].real
+    p32 = obs[:, 3]
+    assert np.abs(p32 - p64).max() <= 1e-6 * np.abs(p64).max()
+    q64 = rows[:, 0].real
+    assert np.abs(obs[:, 1] - q64).max() <= 1e-6 * np.abs(q64).max()
+    assert np.abs(Kg - ref.K.val).max() <= 1e-5 * np.abs(ref.K.val).max()
+    # K stays exactly hermitian by construction
+    assert np.all(obs[:, 9] < 1e-6)
+
+
+def test_mixed_unitarity_excess(rt):
+    s = synth.diamond_system(2, "spd13", 6.0, 6.0)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        ctx = rt.RT(s, precision=prec, **_radii(6.0))
+        ctx.inverse()
+        ctx.propagator(0.0)
+        out[prec] = ctx.unitarity(0, True)
+        ctx.close()
+    assert out["fp32"][0] - out["fp64"][0] <= 1e-8
+    assert out["fp32"][1] - out["fp64"][1] <= 1e-8
