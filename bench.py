@@ -170,6 +170,25 @@ def alu_peaks(torch):
 
 
 # ----------------------------------------------------------------------------
+# ranks (one process per GPU, independent replicas; no data-path collective)
+# ----------------------------------------------------------------------------
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The slowest rank's value (timings are reported as the max over ranks)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps_per_rank: int, max_ms: float, world: int) -> float:
+    """Whole-job steps/s: every rank runs its own replica of the workload, so
+    the job advances world * steps_per_rank steps in the slowest rank's time."""
+    return world * steps_per_rank / (max_ms / 1e3)
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def run_gpu(args):
@@ -219,11 +238,7 @@ def run_gpu(args):
         ctx.step(nsteps)
         ev1.record()
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
         return ms / max(nsteps, 1)
 
     clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv") if os.path.isdir(
@@ -271,11 +286,7 @@ def run_gpu(args):
     ctx_e2e.step(n_e2e)
     obs_e2e = ctx_e2e.observables(0, 0)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     h2d = K1_host.nbytes / n_e2e
     d2h = obs_e2e.nbytes / n_e2e
 
@@ -302,11 +313,11 @@ def run_gpu(args):
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None}
 
-    value_steps = 1e3 / (ms32 if headline_ok else ms64)
+    ms_head = ms32 if headline_ok else ms64
     launches_per_step = (c32 if headline_ok else c64).step_kernels()
     line = {
         "metric": "TDDFT steps/sec & block GFLOP/s vs plain FP64 GPU path at dipole err<=1e-6",
-        "value": round(value_steps * world, 4),
+        "value": round(job_rate(1, ms_head, world), 4),
         "unit": "steps/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -338,7 +349,8 @@ def run_gpu(args):
         "roofline": roof,
         "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                     for k, v in prof[hp].items() if v["launches"]},
-        "e2e": {"value": round(n_e2e / e2e_s * world, 4), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": round(job_rate(n_e2e, e2e_s * 1e3, world), 4), "unit": "steps/s",
+                "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "what": "rt_set_density(K(0+) from host) + rt_step(n) + rt_observables, timed on the host"},
         "gpu_launches": int(round(launches_per_step * args.steps)),
