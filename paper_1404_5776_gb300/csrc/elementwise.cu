@@ -253,59 +253,54 @@ void launch_sum(const double* v, int64_t n, double* part, double sqrt_div, doubl
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
-// Tr(K X) terms: for each block (i,j) of P_K, sum_ab K_ij[a,b] X_ji[b,a] over
-// the true functions; X gathered through kx_map (block (j,i) of X, or -1).
-// Four traces at once: X in {S, Dx, Dy, Dz}; results complex.  One warp per
-// block (coalesced reads of K), fixed block-to-warp assignment, fixed-order
-// reductions: the result does not depend on scheduling.
+// Tr(K X) for X in {S, Dx, Dy, Dz}.  K is hermitian (upper blocks mirrored,
+// diagonal blocks symmetrised) and every X is real symmetric, so
+//   Tr(K X) = sum_{i<j} 2 sum_ab Re K_ij[a,b] X_ji[b,a] + sum_i sum_ab Re K_ii[a,b] X_ii[b,a]
+// and Im Tr(K X) = 0 exactly; only the upper blocks are read.  X_ji comes
+// through kx_map (block (j,i) of X, or -1).  One warp per block (coalesced
+// reads of K), fixed block-to-warp assignment and fixed-order reductions: the
+// result does not depend on scheduling.
 __global__ void k_traces(const double2* __restrict__ K, int64_t nnzb, const int32_t* __restrict__ rowidx,
                          const int32_t* __restrict__ col, const int32_t* __restrict__ bsize, int B,
                          const double* __restrict__ S, const int32_t* __restrict__ ks_map,
                          const double* __restrict__ Dx, const double* __restrict__ Dy, const double* __restrict__ Dz,
                          const int32_t* __restrict__ kd_map, double* __restrict__ part) {
-  __shared__ double s[8][RED_T / 32];
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  __shared__ double s[4][RED_T / 32];
+  double acc[4] = {0, 0, 0, 0};
   const int NE = B * B;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (RED_T / 32) + warp;
   const int64_t nw = (int64_t)gridDim.x * (RED_T / 32);
   for (int64_t q = gw; q < nnzb; q += nw) {
     int i = rowidx[q], j = col[q];
+    if (j < i) continue;
+    const double w = (i == j) ? 1.0 : 2.0;
     int bi = bsize[i], bj = bsize[j];
     int sq = ks_map[q], dq = kd_map[q];
     const double2* k = K + q * NE;
     for (int e = lane; e < bi * bj; e += 32) {
       int a = e / bj, b = e - a * bj;
-      double2 kv = k[a * B + b];
+      double kr = w * k[a * B + b].x;
       int te = b * B + a;  // X_ji[b][a]
-      if (sq >= 0) {
-        double x = S[(int64_t)sq * NE + te];
-        acc[0] += kv.x * x;
-        acc[1] += kv.y * x;
-      }
+      if (sq >= 0) acc[0] += kr * S[(int64_t)sq * NE + te];
       if (dq >= 0) {
-        double x = Dx[(int64_t)dq * NE + te];
-        acc[2] += kv.x * x;
-        acc[3] += kv.y * x;
-        x = Dy[(int64_t)dq * NE + te];
-        acc[4] += kv.x * x;
-        acc[5] += kv.y * x;
-        x = Dz[(int64_t)dq * NE + te];
-        acc[6] += kv.x * x;
-        acc[7] += kv.y * x;
+        acc[1] += kr * Dx[(int64_t)dq * NE + te];
+        acc[2] += kr * Dy[(int64_t)dq * NE + te];
+        acc[3] += kr * Dz[(int64_t)dq * NE + te];
       }
     }
   }
-  for (int c = 0; c < 8; ++c)
+  for (int c = 0; c < 4; ++c)
     for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], off);
   if (lane == 0)
-    for (int c = 0; c < 8; ++c) s[c][warp] = acc[c];
+    for (int c = 0; c < 4; ++c) s[c][warp] = acc[c];
   __syncthreads();
   if (threadIdx.x == 0)
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < 4; ++c) {
       double t = 0.0;
       for (int w = 0; w < RED_T / 32; ++w) t += s[c][w];
-      part[blockIdx.x * 8 + c] = t;
+      part[blockIdx.x * 8 + 2 * c] = t;
+      part[blockIdx.x * 8 + 2 * c + 1] = 0.0;  // Im Tr(K X) = 0 for hermitian K, symmetric X
     }
 }
 

@@ -571,15 +571,19 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
       double cn;
       int ci;
       taylor_coef(n, dt, &cn, &ci);
-      // the last power is needed only inside U: no store of C
-      GemmArgs g = args(s.Tf, prev, n == terms - 1 ? nullptr : bufs[n % 2]);
+      // the last power is needed only inside U: no store of C; its epilogue
+      // also writes (U - I)^dagger per block for the sandwich (13-function
+      // kernels; the generic kernel takes the transpose while staging)
+      const bool last = n == terms - 1;
+      GemmArgs g = args(s.Tf, prev, last ? nullptr : bufs[n % 2]);
       g.U = s.dUf;
       g.coef = cn;
       g.coef_imag = ci;
+      if (last && s.dUH) g.base = s.dUH;
       gemm(c, s, PC_TAYLOR, n == 2 ? t2 : tn, true, false, false, false, EPI_STORE_ACC, g, s.pU);
       prev = bufs[n % 2];
     }
-    if (s.dUH) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
+    if (s.dUH && terms < 3) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
   }
 }
 
@@ -654,8 +658,17 @@ static void sandwich(rt_ctx* c, Sys& s, int kick, int slot) {
   } else {
     // delta form: M = dU K, W = K + M, K' = K + M + W dU^dagger (K, sums in FP64)
     run(c, PC_MISC, 0, 0, [&] { launch_d2f_pad((const double*)K, (float*)s.Kf, s.pK->nnzb, s.B, true, c->ws); });
-    gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUf, s.Kf, s.Mf), s.pM);
-    run(c, PC_MISC, 0, 0, [&] { launch_delta_w(K, s.m_to_k, s.Mf, s.Wf, s.pM->nnzb, s.B, c->ws); });
+    if (s.B == 13) {
+      // M = dU K with W = K + M written by the same epilogue
+      GemmArgs gm = args(s.dUf, s.Kf, s.Mf);
+      gm.base = K;
+      gm.U = s.Wf;
+      gm.add_map = s.m_to_k;
+      gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, gm, s.pM);
+    } else {
+      gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUf, s.Kf, s.Mf), s.pM);
+      run(c, PC_MISC, 0, 0, [&] { launch_delta_w(K, s.m_to_k, s.Mf, s.Wf, s.pM->nnzb, s.B, c->ws); });
+    }
     // 13-function blocks read a pre-transposed (U - I)^dagger; the generic
     // kernel transposes while staging
     const bool pre_t = s.dUH != nullptr;

@@ -85,29 +85,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
-// Issue the TMA copies of one group of NT triples into `buf` (slot k holds
-// A at k*STRIDE and B at k*STRIDE + SB); `ab` holds the group's (a, b) block
-// indices, prefetched one group ahead; triples past the end copy a zero block.
+// Issue the TMA copies of one group of NT triples into `buf` (slot k holds A
+// at k*STRIDE and B at k*STRIDE + SB).  Lane 0 arms the stage's mbarrier with
+// the byte count; then lanes 0..2NT-1 each fetch their triple's block index
+// and issue one bulk copy (all copies in one warp-wide instruction).  Triples
+// past the end copy a zero block.
 template <typename V, int NT>
 __device__ __forceinline__ void issue_group(V* buf, const V* __restrict__ A, const V* __restrict__ B,
-                                            const int2 (&ab)[NT], int64_t tb, int64_t t1,
-                                            const V* __restrict__ zero, uint64_t* bar) {
+                                            const int2* __restrict__ ab, int64_t tb, int64_t t1,
+                                            const V* __restrict__ zero, uint64_t* bar, int lane) {
   constexpr unsigned BYTES = SB * sizeof(V);
-  mbar_expect_tx(bar, NT * 2 * BYTES);
-#pragma unroll
-  for (int k = 0; k < NT; ++k) {
-    const bool valid = tb + k < t1;
-    const V* pa = valid ? A + (int64_t)ab[k].x * SB : zero;
-    const V* pb = valid ? B + (int64_t)ab[k].y * SB : zero;
-    tma_load_1d(buf + k * Slot<V>::STRIDE, pa, BYTES, bar);
-    tma_load_1d(buf + k * Slot<V>::STRIDE + SB, pb, BYTES, bar);
+  if (lane == 0) mbar_expect_tx(bar, NT * 2 * BYTES);
+  __syncwarp();
+  if (lane < 2 * NT) {
+    const int k = lane >> 1;
+    const bool isB = lane & 1;
+    const int64_t t = tb + k;
+    const V* src = zero;
+    if (t < t1) {
+      const int2 p = ab[t];
+      src = isB ? B + (int64_t)p.y * SB : A + (int64_t)p.x * SB;
+    }
+    tma_load_1d(buf + k * Slot<V>::STRIDE + (isB ? SB : 0), src, BYTES, bar);
   }
-}
-
-template <int NT>
-__device__ __forceinline__ void load_ab(int2 (&ab)[NT], const int2* __restrict__ src, int64_t tb, int64_t t1) {
-#pragma unroll
-  for (int k = 0; k < NT; ++k) ab[k] = (tb + k < t1) ? src[tb + k] : make_int2(0, 0);
 }
 
 struct Smem {
@@ -151,21 +151,13 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
   unsigned pending = 0u;  // bit s: copies in flight into stage s
   bool ok = true;
   int stage = 0;
-  int2 nab[NT];  // (a, b) indices of the next group to issue (lane 0)
   if (t0 < t1) {
-    if (lane == 0) {
-      load_ab<NT>(nab, g.ab, t0, t1);
-      issue_group<float2, NT>(wsm, A, B, nab, t0, t1, Z, &bar[0]);
-      load_ab<NT>(nab, g.ab, t0 + NT, t1);
-    }
+    issue_group<float2, NT>(wsm, A, B, g.ab, t0, t1, Z, &bar[0], lane);
     pending |= 1u;
   }
   for (int64_t tb = t0; tb < t1; tb += NT) {
     if (tb + NT < t1) {
-      if (lane == 0) {
-        issue_group<float2, NT>(wsm + (stage ^ 1) * WBUF, A, B, nab, tb + NT, t1, Z, &bar[stage ^ 1]);
-        load_ab<NT>(nab, g.ab, tb + 2 * NT, t1);  // consumed one iteration later
-      }
+      issue_group<float2, NT>(wsm + (stage ^ 1) * WBUF, A, B, g.ab, tb + NT, t1, Z, &bar[stage ^ 1], lane);
       pending |= 1u << (stage ^ 1);
     }
     if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
@@ -214,6 +206,22 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
     if (h == 0 && c < BS) {
 #pragma unroll
       for (int r = 0; r < BS; ++r) C[(int64_t)q * SB + r * RS + c] = acc[r];
+    }
+    // delta form: also W = K + M in FP32 (K in FP64, dense blocks, through
+    // the map from this pattern to K's; -1 = no K block)
+    if (g.base) {
+      const double2* __restrict__ Kb = static_cast<const double2*>(g.base);
+      float2* __restrict__ W = static_cast<float2*>(g.U);
+      const int kq = g.add_map ? g.add_map[q] : q;
+      if (h == 0 && c < BS) {
+        double2 kv[BS];
+#pragma unroll
+        for (int r = 0; r < BS; ++r) kv[r] = (kq >= 0) ? Kb[(int64_t)kq * NE + r * BS + c] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < BS; ++r)
+          W[(int64_t)q * SB + r * RS + c] =
+              make_float2((float)((double)acc[r].x + kv[r].x), (float)((double)acc[r].y + kv[r].y));
+      }
     }
   } else if constexpr (EPI == EPI_DELTA_SANDWICH) {
     // K'_ij = K_ij + M_ij + acc for j >= i (K in FP64, NE layout); mirror;
@@ -310,21 +318,13 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_r32(GemmArgs g) {
   unsigned pending = 0u;  // bit s: copies in flight into stage s
   bool ok = true;
   int stage = 0;
-  int2 nab[NT];  // (a, b) indices of the next group to issue (lane 0)
   if (t0 < t1) {
-    if (lane == 0) {
-      load_ab<NT>(nab, g.ab, t0, t1);
-      issue_group<float, NT>(wsm, A, B, nab, t0, t1, Z, &bar[0]);
-      load_ab<NT>(nab, g.ab, t0 + NT, t1);
-    }
+    issue_group<float, NT>(wsm, A, B, g.ab, t0, t1, Z, &bar[0], lane);
     pending |= 1u;
   }
   for (int64_t tb = t0; tb < t1; tb += NT) {
     if (tb + NT < t1) {
-      if (lane == 0) {
-        issue_group<float, NT>(wsm + (stage ^ 1) * WBUF, A, B, nab, tb + NT, t1, Z, &bar[stage ^ 1]);
-        load_ab<NT>(nab, g.ab, tb + 2 * NT, t1);  // consumed one iteration later
-      }
+      issue_group<float, NT>(wsm + (stage ^ 1) * WBUF, A, B, g.ab, tb + NT, t1, Z, &bar[stage ^ 1], lane);
       pending |= 1u << (stage ^ 1);
     }
     if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
@@ -414,6 +414,15 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_r32(GemmArgs g) {
         float2* dst = &U[(int64_t)uq * SB + r * RS + c0];
         if (c1 < BS) *reinterpret_cast<float4*>(dst) = uv[r];
         else *dst = make_float2(uv[r].x, uv[r].y);
+      }
+      // last power: U is complete; also write its conjugate transpose per block
+      if (g.base) {
+        float2* __restrict__ UH = static_cast<float2*>(const_cast<void*>(g.base));
+#pragma unroll
+        for (int r = 0; r < BS; ++r) {
+          UH[(int64_t)uq * SB + c0 * RS + r] = make_float2(uv[r].x, -uv[r].y);
+          if (c1 < BS) UH[(int64_t)uq * SB + c1 * RS + r] = make_float2(uv[r].z, -uv[r].w);
+        }
       }
     }
     if (C) {
