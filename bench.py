@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--foe-order", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
+    ap.add_argument("--precision-study", type=int, default=0, metavar="NSTEPS",
+                    help="instead of timing: run both paths NSTEPS steps and report their agreement")
     return ap.parse_args()
 
 
@@ -440,8 +442,57 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def precision_study(args):
+    """Mixed (FP32 products) vs FP64 path over many steps from the same K(0+):
+    dipole error relative to |P| and to the induced amplitude, charge
+    difference, and the S-unitarity error of both propagators."""
+    import paper_1404_5776_gb300 as rtm
+    rtm.build()
+    s = workload(args)
+    mu, e_lo, e_hi = model_spectrum(args)
+    R = args.radius
+    common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=args.precision_study + 8,
+                  r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
+    c64 = rtm.RT(s, precision="fp64", **common)
+    c64.inverse()
+    c64.ground_state(0, args.foe_order, mu, 0.01, e_lo, e_hi)
+    c64.kick(0, 0, 0, 1e-3)
+    K1 = c64.matrix(0, rtm.RT_MAT_K)
+    c32 = rtm.RT(s, precision="fp32", **common)
+    c32.inverse()
+    c32.set_density(0, 0, K1)
+    t0 = time.perf_counter()
+    c64.step(args.precision_study)
+    o64 = c64.observables(0, 0)
+    t64 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    c32.step(args.precision_study)
+    o32 = c32.observables(0, 0)
+    t32 = time.perf_counter() - t0
+    u64 = c64.unitarity(0, True)
+    u32 = c32.unitarity(0, True)
+    p64, p32 = o64[:, 3], o32[:, 3]
+    ind = np.abs(p64 - p64[0]).max()
+    out = {"study": "precision", "workload": cfg_name(args), "steps": args.precision_study,
+           "dipole_err_rel_P": float(np.abs(p32 - p64).max() / np.abs(p64).max()),
+           "dipole_err_rel_induced": float(np.abs(p32 - p64).max() / ind) if ind > 0 else None,
+           "induced_amplitude_rel_P": float(ind / np.abs(p64).max()),
+           "trks_diff_rel": float(np.abs(o32[:, 1] - o64[:, 1]).max() / abs(o64[0, 1])),
+           "trks_drift_fp64_rel": float(np.abs(o64[:, 1] - o64[0, 1]).max() / abs(o64[0, 1])),
+           "trks_drift_mixed_rel": float(np.abs(o32[:, 1] - o32[0, 1]).max() / abs(o32[0, 1])),
+           "unitarity_fp64": {"max": u64[0], "mean": u64[1]}, "unitarity_mixed": {"max": u32[0], "mean": u32[1]},
+           "unitarity_excess_max": u32[0] - u64[0], "wall_s": {"fp64": t64, "mixed": t32},
+           "dipole_trace_every_100": [[float(a), float(b)] for a, b in zip(p64[::100], p32[::100])]}
+    c64.close()
+    c32.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.precision_study:
+        precision_study(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -87,12 +87,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 
 // Issue the TMA copies of one group of NT triples into `buf` (slot k holds A
 // at k*STRIDE and B at k*STRIDE + SB).  Lane 0 arms the stage's mbarrier with
-// the byte count; then lanes 0..2NT-1 each fetch their triple's block index
-// and issue one bulk copy (all copies in one warp-wide instruction).  Triples
-// past the end copy a zero block.
+// the byte count; then lanes 0..2NT-1 issue one bulk copy each (all copies in
+// one warp-wide instruction).  `blk` is the lane's block index for this group,
+// loaded one group ahead (-1: past the end, copy a zero block).
 template <typename V, int NT>
-__device__ __forceinline__ void issue_group(V* buf, const V* __restrict__ A, const V* __restrict__ B,
-                                            const int2* __restrict__ ab, int64_t tb, int64_t t1,
+__device__ __forceinline__ void issue_group(V* buf, const V* __restrict__ A, const V* __restrict__ B, int blk,
                                             const V* __restrict__ zero, uint64_t* bar, int lane) {
   constexpr unsigned BYTES = SB * sizeof(V);
   if (lane == 0) mbar_expect_tx(bar, NT * 2 * BYTES);
@@ -100,14 +99,19 @@ __device__ __forceinline__ void issue_group(V* buf, const V* __restrict__ A, con
   if (lane < 2 * NT) {
     const int k = lane >> 1;
     const bool isB = lane & 1;
-    const int64_t t = tb + k;
-    const V* src = zero;
-    if (t < t1) {
-      const int2 p = ab[t];
-      src = isB ? B + (int64_t)p.y * SB : A + (int64_t)p.x * SB;
-    }
+    const V* src = blk < 0 ? zero : (isB ? B : A) + (int64_t)blk * SB;
     tma_load_1d(buf + k * Slot<V>::STRIDE + (isB ? SB : 0), src, BYTES, bar);
   }
+}
+
+// The block index lane `lane` (< 2NT) copies for the group starting at tb.
+template <int NT>
+__device__ __forceinline__ int group_block(const int2* __restrict__ ab, int64_t tb, int64_t t1, int lane) {
+  if (lane >= 2 * NT) return -1;
+  const int64_t t = tb + (lane >> 1);
+  if (t >= t1) return -1;
+  const int2 p = ab[t];
+  return (lane & 1) ? p.y : p.x;
 }
 
 struct Smem {
@@ -151,13 +155,16 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
   unsigned pending = 0u;  // bit s: copies in flight into stage s
   bool ok = true;
   int stage = 0;
+  int nblk = -1;  // this lane's block index for the next group (prefetched)
   if (t0 < t1) {
-    issue_group<float2, NT>(wsm, A, B, g.ab, t0, t1, Z, &bar[0], lane);
+    issue_group<float2, NT>(wsm, A, B, group_block<NT>(g.ab, t0, t1, lane), Z, &bar[0], lane);
+    nblk = group_block<NT>(g.ab, t0 + NT, t1, lane);
     pending |= 1u;
   }
   for (int64_t tb = t0; tb < t1; tb += NT) {
     if (tb + NT < t1) {
-      issue_group<float2, NT>(wsm + (stage ^ 1) * WBUF, A, B, g.ab, tb + NT, t1, Z, &bar[stage ^ 1], lane);
+      issue_group<float2, NT>(wsm + (stage ^ 1) * WBUF, A, B, nblk, Z, &bar[stage ^ 1], lane);
+      nblk = group_block<NT>(g.ab, tb + 2 * NT, t1, lane);  // used one iteration later
       pending |= 1u << (stage ^ 1);
     }
     if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
@@ -318,13 +325,16 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_r32(GemmArgs g) {
   unsigned pending = 0u;  // bit s: copies in flight into stage s
   bool ok = true;
   int stage = 0;
+  int nblk = -1;  // this lane's block index for the next group (prefetched)
   if (t0 < t1) {
-    issue_group<float, NT>(wsm, A, B, g.ab, t0, t1, Z, &bar[0], lane);
+    issue_group<float, NT>(wsm, A, B, group_block<NT>(g.ab, t0, t1, lane), Z, &bar[0], lane);
+    nblk = group_block<NT>(g.ab, t0 + NT, t1, lane);
     pending |= 1u;
   }
   for (int64_t tb = t0; tb < t1; tb += NT) {
     if (tb + NT < t1) {
-      issue_group<float, NT>(wsm + (stage ^ 1) * WBUF, A, B, g.ab, tb + NT, t1, Z, &bar[stage ^ 1], lane);
+      issue_group<float, NT>(wsm + (stage ^ 1) * WBUF, A, B, nblk, Z, &bar[stage ^ 1], lane);
+      nblk = group_block<NT>(g.ab, tb + 2 * NT, t1, lane);  // used one iteration later
       pending |= 1u << (stage ^ 1);
     }
     if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
