@@ -242,6 +242,39 @@ RT_API rt_status rt_profile_read(rt_ctx* ctx, int32_t max, int32_t* n_classes, i
 RT_API rt_status rt_get_state(rt_ctx* ctx, void* buf, size_t* bytes);
 RT_API rt_status rt_set_state(rt_ctx* ctx, const void* buf, size_t bytes);
 
+/* Allocation-free traces.  The paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory when they need the
+ * observables -- code running while a stream is being captured into a CUDA
+ * graph (allocation is not allowed there) or a host framework that owns all
+ * device memory.  It allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library call) and needs no context.
+ *
+ * Computes out[0..7] = (Re, Im) of Tr(K S), Tr(K Dx), Tr(K Dy), Tr(K Dz) for a
+ * hermitian K and real symmetric S, D (the imaginary parts are then 0), from
+ * the upper blocks of K, exactly as rt_observables does.  All pointers are
+ * device memory owned by the caller:
+ *   K       nnzb blocks of B x B complex values (interleaved re, im doubles),
+ *           row-major, in pattern order; rowidx[q], col[q] = block (i,j)
+ *   bsize   [n_atoms] true functions per atom (<= B; the rest is padding)
+ *   S       real B x B blocks; ks_map[q] = index in S of block (j,i), or -1
+ *   Dx,Dy,Dz real B x B blocks on one pattern; kd_map[q] = index of (j,i), or -1
+ *   out     [8] doubles
+ * n_ctas: CTAs of the partial-sum pass (0 = automatic); at most
+ * RT_NOALLOC_MAX_CTAS, larger values are rejected with RT_EINVAL.
+ * Scratch: a fixed device array of RT_NOALLOC_MAX_CTAS * 8 doubles (64 KiB)
+ * inside the library, held by every GPU that loads it until the process
+ * exits; nothing in it needs to start at zero.  All calls share it, so calls
+ * that overlap on the GPU race: serialise them.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and should come
+ * before any stream capture.  Work is enqueued on cuda_stream (NULL = legacy
+ * default stream); the call does not synchronise.  Errors: RT_EINVAL, RT_ECUDA
+ * (reason printed on stderr). */
+#define RT_NOALLOC_MAX_CTAS 1024
+RT_API rt_status rt_traces_noalloc(const double* K, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
+                                   const int32_t* bsize, int32_t B, const double* S, const int32_t* ks_map,
+                                   const double* Dx, const double* Dy, const double* Dz, const int32_t* kd_map,
+                                   int32_t n_ctas, double* out, void* cuda_stream);
+
 /* Waits for all work of the context's stream. */
 RT_API rt_status rt_synchronize(rt_ctx* ctx);
 

@@ -37,7 +37,7 @@ OBS_FIELDS = ["t", "trks_re", "trks_im", "trkdx_re", "trkdx_im", "trkdy_re", "tr
 EXPORTED = ["rt_default_params", "rt_create", "rt_set_field", "rt_inverse", "rt_set_density", "rt_ground_state",
             "rt_kick", "rt_propagator", "rt_step", "rt_observables", "rt_pattern_size", "rt_get_pattern",
             "rt_matrix_size", "rt_get_matrix", "rt_unitarity", "rt_step_work", "rt_step_kernels", "rt_profile", "rt_profile_read",
-            "rt_get_state", "rt_set_state", "rt_synchronize", "rt_last_error", "rt_destroy"]
+            "rt_get_state", "rt_set_state", "rt_synchronize", "rt_last_error", "rt_destroy", "rt_traces_noalloc"]
 
 
 class rt_system(ctypes.Structure):
@@ -106,6 +106,7 @@ def load(path: Optional[str] = None):
         "rt_get_state": [P, P, P],
         "rt_set_state": [P, P, ctypes.c_size_t],
         "rt_synchronize": [P],
+        "rt_traces_noalloc": [P, I64, P, P, P, I32, P, P, P, P, P, P, I32, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
