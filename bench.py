@@ -225,6 +225,19 @@ def run_gpu(args):
     c32.inverse()
     c32.set_density(0, 0, K1)
 
+    # propagation-step contexts (U built once; the delta kick leaves H constant):
+    # FP64, and FP32 in the incremental form dK = K - K_ref
+    c64p = rtm.RT(s, precision="fp64", full_step=0, **common)
+    c64p.inverse()
+    c64p.set_density(0, 0, K1)
+    c64p.propagator(0.0)
+    c32i = None
+    if args.basis == "spd13":
+        c32i = rtm.RT(s, precision="fp32", full_step=0, incremental=1, **common)
+        c32i.inverse()
+        c32i.set_density(0, 0, K1)
+        c32i.propagator(0.0)
+
     n64 = args.fp64_steps if args.fp64_steps is not None else args.steps
     res = {}
 
@@ -248,6 +261,8 @@ def run_gpu(args):
     clocks.start()
     ms64 = timed(c64, n64, args.warmup)
     ms32 = timed(c32, args.steps, args.warmup)
+    ms64p = timed(c64p, n64, args.warmup)
+    ms32i = timed(c32i, args.steps, args.warmup) if c32i else float("nan")
     clk = clocks.stop()
 
     flops64, bytes64 = c64.step_work()
@@ -264,6 +279,13 @@ def run_gpu(args):
     trks_drift32 = float(np.abs(o32[:, 1] - o32[0, 1]).max() / abs(o32[0, 1])) if len(o32) else float("nan")
     trks_drift64 = float(np.abs(o64[:, 1] - o64[0, 1]).max() / abs(o64[0, 1])) if len(o64) else float("nan")
     trks_diff = float(np.abs(o32[:m, 1] - o64[:m, 1]).max() / abs(o64[0, 1])) if m else float("nan")
+    # propagation-step pair: FP32 incremental vs FP64 from the same K(0+)
+    o64p = c64p.observables(0, 0)
+    o32i = c32i.observables(0, 0) if c32i else o64p[:0]
+    mi = min(len(o64p), len(o32i))
+    dip_i = float(np.abs(o32i[:mi, 3] - o64p[:mi, 3]).max() / np.abs(o64p[:mi, 3]).max()) if mi else float("nan")
+    ind_p = np.abs(o64p[:mi, 3] - o64p[0, 3]).max() if mi else float("nan")
+    dip_i_ind = float(np.abs(o32i[:mi, 3] - o64p[:mi, 3]).max() / ind_p) if mi and ind_p > 0 else float("nan")
 
     # per-kernel-class times (CUDA events on the library stream), a short extra pass
     prof = {}
@@ -339,6 +361,13 @@ def run_gpu(args):
             "fp32_mixed": {"ms_per_step": round(ms32, 3), "steps_per_s": round(1e3 / ms32, 4),
                            "gflops": round(flops32 / (ms32 / 1e3) / 1e9, 2), "timed_steps": args.steps},
             "speedup_mixed_vs_fp64": round(ms64 / ms32, 2),
+            "propagation_step": {
+                "what": "delta kick: H is constant for t > 0, U built once (FP64) and reused; sandwich + traces per step",
+                "fp64": {"ms_per_step": round(ms64p, 3), "steps_per_s": round(1e3 / ms64p, 4)},
+                "fp32_incremental": {"ms_per_step": round(ms32i, 3), "steps_per_s": round(1e3 / ms32i, 4),
+                                     "dipole_rel_err_vs_fp64": dip_i, "dipole_err_rel_to_induced": dip_i_ind,
+                                     "compared_steps": int(mi)} if c32i else None,
+                "speedup_incremental_vs_fp64": round(ms64p / ms32i, 2) if c32i else None},
             "algorithmic_flops_per_step": flops64,
             "dipole_rel_err_mixed_vs_fp64": dip_rel,
             "dipole_err_rel_to_induced": dip_rel_ind,
@@ -361,8 +390,14 @@ def run_gpu(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, s, budget_s=20.0)
-    c64.close()
-    c32.close()
+    line["gate"] = {
+        "reading": "dipole error relative to |P| (max_t |P_mixed - P_fp64| / max_t |P_fp64|) <= 1e-6",
+        "headline_passes": bool(headline_ok),
+        "induced_amplitude_reading": {"full_step_mixed": dip_rel_ind,
+                                      "propagation_step_incremental": dip_i_ind if c32i else None}}
+    for ctx in (c64, c32, c64p, c32i):
+        if ctx:
+            ctx.close()
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -134,6 +134,11 @@ typedef struct {
   int32_t kick_terms;       /* Taylor terms of the kick exponential               */
   int32_t obs_capacity;     /* steps kept in the observables buffer               */
   int32_t use_graph;        /* capture the step in a CUDA graph and replay it     */
+  int32_t incremental;      /* with RT_FP32 and full_step = 0 (constant U, built in
+                               FP64): propagate dK = K - K_ref, K_ref = K at the
+                               first step after K or U changed, with
+                               R = U K_ref U^dagger - K_ref in FP64 and U - I as
+                               FP32 hi + lo; 13-function systems only          */
 } rt_params;
 
 typedef struct {
@@ -144,7 +149,7 @@ typedef struct {
 
 /* Fills the defaults: radii 8 A, dt 0.05, EM, 6 Taylor terms, tol 1e-10,
  * maxit 100, 2 CN iterations per step, FP64, full step, 1 kick, 12 kick terms,
- * 4096 observable steps, graphs on. */
+ * 4096 observable steps, graphs on, incremental form off. */
 RT_API rt_status rt_default_params(rt_params* p);
 
 /* Creates a context for n_sys systems: validates and copies the host inputs,

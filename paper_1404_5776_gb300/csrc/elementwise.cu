@@ -306,7 +306,8 @@ __global__ void k_traces(const double2* __restrict__ K, int64_t nnzb, const int3
 
 // Sums the trace partials in fixed order and writes one observables record.
 __global__ void k_traces_final(const double* __restrict__ part, int nb, const DevState* st, int herm_slot,
-                               double* __restrict__ ring, int capacity, int n_slots, int slot_index) {
+                               double* __restrict__ ring, int capacity, int n_slots, int slot_index,
+                               const double* __restrict__ ref, double* __restrict__ out) {
   __shared__ double s[8][RED_T];
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < nb; i += RED_T)
@@ -317,6 +318,12 @@ __global__ void k_traces_final(const double* __restrict__ part, int nb, const De
     if (threadIdx.x < off)
       for (int c = 0; c < 8; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + off];
     __syncthreads();
+  }
+  if (threadIdx.x == 0 && ref)  // incremental form: traces of K_ref + dK
+    for (int c = 0; c < 8; ++c) s[c][0] += ref[c];
+  if (threadIdx.x == 0 && out) {  // plain output (reference traces)
+    for (int c = 0; c < 8; ++c) out[c] = s[c][0];
+    return;
   }
   if (threadIdx.x == 0) {
     int64_t step = st->step - 1;  // runs after the step counter advanced
@@ -341,10 +348,11 @@ __global__ void k_traces_final(const double* __restrict__ part, int nb, const De
 void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const int32_t* col, const int32_t* bsize,
                    int B, const double* S, const int32_t* ks_map, const double* Dx, const double* Dy,
                    const double* Dz, const int32_t* kd_map, double* part, const DevState* st, int herm_slot,
-                   double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s) {
+                   double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s, const double* ref,
+                   double* out) {
   int nb = reduce_blocks(nnzb);
   k_traces<<<nb, RED_T, 0, s>>>(K, nnzb, rowidx, col, bsize, B, S, ks_map, Dx, Dy, Dz, kd_map, part);
-  k_traces_final<<<1, RED_T, 0, s>>>(part, nb, st, herm_slot, ring, capacity, n_slots, slot_index);
+  k_traces_final<<<1, RED_T, 0, s>>>(part, nb, st, herm_slot, ring, capacity, n_slots, slot_index, ref, out);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -643,6 +651,54 @@ void launch_u_from_delta(const float2* dU, double2* U, int64_t nnzb, const int32
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
   k_u_from_delta<<<(unsigned)g, 256, 0, st>>>(dU, U, nnzb, rowidx, col, B, rs32(B));
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// Incremental form: U - I split into FP32 hi + lo parts (FP32 block layout),
+// so that hi + lo carries U - I to about 2^-48 relative.
+__global__ void k_split_u_hilo(const double2* __restrict__ U, float2* __restrict__ hi, float2* __restrict__ lo,
+                               int64_t nnzb, const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B,
+                               int rs) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int r = e / B, c = e - r * B;
+    double2 u = U[idx];
+    double dr = u.x - ((rowidx[q] == col[q] && r == c) ? 1.0 : 0.0), di = u.y;
+    float hr = (float)dr, hi_ = (float)di;
+    int64_t o = q * (int64_t)B * rs + r * rs + c;
+    hi[o] = make_float2(hr, hi_);
+    lo[o] = make_float2((float)(dr - (double)hr), (float)(di - (double)hi_));
+  }
+}
+
+void launch_split_u_hilo(const double2* U, float2* hi, float2* lo, int64_t nnzb, const int32_t* rowidx,
+                         const int32_t* col, int B, cudaStream_t st) {
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_split_u_hilo<<<(unsigned)g, 256, 0, st>>>(U, hi, lo, nnzb, rowidx, col, B, rs32(B));
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// z = x + a*y (complex FP64 vectors of n elements)
+__global__ void k_zaxpy(double2* __restrict__ z, const double2* __restrict__ x, const double2* __restrict__ y, double a,
+                        int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 xv = x[i], yv = y[i];
+    z[i] = make_double2(xv.x + a * yv.x, xv.y + a * yv.y);
+  }
+}
+
+void launch_zaxpy(double2* z, const double2* x, const double2* y, double a, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_zaxpy<<<(unsigned)g, 256, 0, st>>>(z, x, y, a, n);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -71,6 +71,11 @@ struct Sys {
   // FP32 buffers (mixed precision)
   float *Tf = nullptr, *Pf0 = nullptr, *Pf1 = nullptr;
   float2 *dUf = nullptr, *dUH = nullptr, *Kf = nullptr, *Mf = nullptr, *Wf = nullptr;
+  // incremental form (FP32, constant U): K = K_ref + dK, R = U K_ref U^dagger - K_ref
+  std::vector<double2*> Kref, dK, Rm;
+  std::vector<double*> tref;      // reference traces (8 doubles per kick)
+  std::vector<char> ref_fresh;    // dK holds K - K_ref for this kick (K itself is stale)
+  float2 *dUh = nullptr, *dUl = nullptr, *dUHh = nullptr, *dUHl = nullptr, *Nf = nullptr, *Mlo = nullptr;
   // maps
   int32_t *u_to_t = nullptr, *a_to_s = nullptr, *a_to_h = nullptr, *k_to_sT = nullptr, *k_to_hT = nullptr;
   int32_t *u_to_sinv = nullptr, *k_to_sinv = nullptr, *u_to_s = nullptr, *k_to_m = nullptr, *m_to_k = nullptr;
@@ -226,6 +231,7 @@ static TripleInfo& triples_for(rt_ctx* c, Sys& s, Pattern* A, bool ad, Pattern* 
 }
 
 static size_t nvals(const Sys& s, const Pattern* P) { return (size_t)P->nnzb * s.B * s.B; }
+static bool incremental(const rt_ctx* c) { return c->p.incremental != 0; }
 // elements of an FP32 matrix (13-function blocks padded to 13 x 16)
 static size_t nvals32(const Sys& s, const Pattern* P) { return (size_t)P->nnzb * sb32(s.B); }
 
@@ -448,6 +454,31 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
       s.TD = c->arena.get_n<double>(nvals(s, s.pT));
     }
   }
+  if (p.incremental) {
+    // incremental form for a constant propagator (13-function blocks)
+    RT_REQUIRE(s.B == 13, RT_EINVAL, "the incremental form needs 13-function atoms (block size 13)");
+    for (int k = 0; k < p.n_kick; ++k) {
+      s.Kref.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
+      s.dK.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
+      s.Rm.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
+      s.tref.push_back(c->arena.get_n<double>(8));
+    }
+    s.ref_fresh.assign(p.n_kick, 0);
+    s.dUh = c->arena.get_n<float2>(nvals32(s, s.pU));
+    s.dUl = c->arena.get_n<float2>(nvals32(s, s.pU));
+    s.Nf = c->arena.get_n<float2>(nvals32(s, s.pK));
+    s.Mlo = c->arena.get_n<float2>(nvals32(s, s.pM));
+    RT_CUDA_CHECK(cudaMemsetAsync(s.Mlo, 0, sizeof(float2) * nvals32(s, s.pM), c->ws));
+    RT_CUDA_CHECK(cudaMemsetAsync(s.dUh, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+    RT_CUDA_CHECK(cudaMemsetAsync(s.dUl, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+    RT_CUDA_CHECK(cudaMemsetAsync(s.Nf, 0, sizeof(float2) * nvals32(s, s.pK), c->ws));
+    if (s.B == 13) {
+      s.dUHh = c->arena.get_n<float2>(nvals32(s, s.pU));
+      s.dUHl = c->arena.get_n<float2>(nvals32(s, s.pU));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.dUHh, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.dUHl, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+    }
+  }
   RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
 }
 
@@ -587,10 +618,9 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
   }
 }
 
-static void build_propagator(rt_ctx* c, Sys& s) {
+static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
   const rt_params& p = c->p;
   const int dir = c->field.dir;
-  const bool fp32 = p.precision == RT_FP32;
   if (p.prop == RT_PROP_EM) {
     if (fp32) {
       // T(t+dt/2) = T0 - E T_D (linearity of the cut product in E)
@@ -683,14 +713,74 @@ static void sandwich(rt_ctx* c, Sys& s, int kick, int slot) {
 
 static void observe(rt_ctx* c, Sys& s, int kick, int slot) {
   double bytes = 16.0 * nvals(s, s.pK) + 8.0 * 4 * nvals(s, s.pH);
+  const bool incr = incremental(c);
   run(
       c, PC_OBS, 0, bytes,
       [&] {
-        launch_traces(s.K[kick], s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S, s.k_to_sT, s.D[0], s.D[1],
-                      s.D[2], s.k_to_hT, s.red_part, c->dstate, slot, c->ring, c->p.obs_capacity, c->n_slots, slot,
-                      c->ws);
+        launch_traces(incr ? s.dK[kick] : s.K[kick], s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S,
+                      s.k_to_sT, s.D[0], s.D[1], s.D[2], s.k_to_hT, s.red_part, c->dstate, slot, c->ring,
+                      c->p.obs_capacity, c->n_slots, slot, c->ws, incr ? s.tref[kick] : nullptr, nullptr);
       },
       2);
+}
+
+// K = K_ref + dK for kicks whose K is stale (before K is read or replaced)
+static void materialize(rt_ctx* c, Sys& s) {
+  for (size_t k = 0; k < s.ref_fresh.size(); ++k) {
+    if (!s.ref_fresh[k]) continue;
+    launch_zaxpy(s.K[k], s.Kref[k], s.dK[k], 1.0, (int64_t)nvals(s, s.pK), c->ws);
+    s.ref_fresh[k] = 0;
+  }
+}
+
+// K_ref = K, dK = 0, R = cut(cut(U K_ref) U^dagger) - K_ref (FP64 sandwich),
+// reference traces Tr(K_ref X)
+static void make_reference(rt_ctx* c, Sys& s, int kick) {
+  const size_t nv = nvals(s, s.pK);
+  RT_CUDA_CHECK(cudaMemcpyAsync(s.Kref[kick], s.K[kick], sizeof(double2) * nv, cudaMemcpyDeviceToDevice, c->ws));
+  RT_CUDA_CHECK(cudaMemsetAsync(s.dK[kick], 0, sizeof(double2) * nv, c->ws));
+  TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
+  TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
+  gemm(c, s, PC_MISC, tM, false, true, false, false, EPI_STORE, args(s.U, s.Kref[kick], s.M), s.pM);
+  gemm(c, s, PC_MISC, tK, false, true, false, true, EPI_SANDWICH, args(s.M, s.U, s.Rm[kick]), s.pK);
+  launch_zaxpy(s.Rm[kick], s.Rm[kick], s.Kref[kick], -1.0, (int64_t)nv, c->ws);
+  launch_traces(s.Kref[kick], s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S, s.k_to_sT, s.D[0], s.D[1],
+                s.D[2], s.k_to_hT, s.red_part, c->dstate, 0, c->ring, c->p.obs_capacity, c->n_slots, 0, c->ws, nullptr,
+                s.tref[kick]);
+  s.ref_fresh[kick] = 1;
+}
+
+// dK' = dK + R + M + N with M = M_hi + M_lo = (dU_hi + dU_lo) dK, W = dK + M,
+// N = N_hi + N_lo = W (dU_hi + dU_lo)^dagger: four FP32 products, every part
+// kept separately and summed in FP64 (13-function blocks).
+static void sandwich_incremental(rt_ctx* c, Sys& s, int kick, int slot) {
+  TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
+  TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
+  double2* dK = s.dK[kick];
+  run(c, PC_MISC, 0, 0, [&] { launch_d2f_pad((const double*)dK, (float*)s.Kf, s.pK->nnzb, s.B, true, c->ws); });
+  gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUh, s.Kf, s.Mf), s.pM);
+  TripleInfo tMl = tM;  // the lo halves are precision bookkeeping: no algorithmic flops
+  tMl.true_macs = 0;
+  {
+    GemmArgs g = args(s.dUl, s.Kf, s.Mlo);
+    g.base = dK;       // W = dK + (M_hi + M_lo) from the same epilogue
+    g.addend = s.Mf;
+    g.U = s.Wf;
+    g.add_map = s.m_to_k;
+    gemm(c, s, PC_UK, tMl, true, true, false, false, EPI_STORE, g, s.pM);
+  }
+  TripleInfo tKl = tK;
+  tKl.true_macs = 0;
+  gemm(c, s, PC_MUDAG, tKl, true, true, false, false, EPI_STORE, args(s.Wf, s.dUHl, s.Nf), s.pK);
+  GemmArgs g = args(s.Wf, s.dUHh, dK);
+  g.herm_max = &c->dstate->herm_bits[slot];
+  g.base = dK;
+  g.addend = s.Mf;
+  g.addend3 = s.Mlo;
+  g.add_map = s.k_to_m;
+  g.base2 = s.Rm[kick];
+  g.addend2 = s.Nf;
+  gemm(c, s, PC_MUDAG, tK, true, true, false, false, EPI_DELTA_SANDWICH, g, s.pK);
 }
 
 static void enqueue_step(rt_ctx* c) {
@@ -698,8 +788,11 @@ static void enqueue_step(rt_ctx* c) {
   int slot = 0;
   for (auto& sp : c->sys) {
     Sys& s = *sp;
-    if (c->p.full_step) build_propagator(c, s);
-    for (int k = 0; k < c->p.n_kick; ++k) sandwich(c, s, k, slot + k);
+    if (c->p.full_step) build_propagator(c, s, c->p.precision == RT_FP32);
+    for (int k = 0; k < c->p.n_kick; ++k) {
+      if (incremental(c)) sandwich_incremental(c, s, k, slot + k);
+      else sandwich(c, s, k, slot + k);
+    }
     slot += c->p.n_kick;
   }
   run(c, PC_MISC, 0, 0, [&] { launch_end_step(c->dstate, c->p.dt, c->ws); });
@@ -797,7 +890,7 @@ static void ensure_unitarity_lists(rt_ctx* c, Sys& s) {
 
 static void unitarity(rt_ctx* c, Sys& s, int metric, double* mx, double* mean) {
   ensure_unitarity_lists(c, s);
-  if (c->p.precision == RT_FP32 && c->p.prop == RT_PROP_EM)
+  if (c->p.precision == RT_FP32 && c->p.prop == RT_PROP_EM && !c->p.incremental)
     launch_u_from_delta(s.dUf, s.U, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);  // U = I + dU
   if (metric) {
     TripleInfo& tW = triples_for(c, s, s.pS, false, s.pU, false, s.pW, false);
@@ -960,6 +1053,8 @@ rt_status rt_create(rt_ctx** out, const rt_system* sys, int32_t n_sys, const rt_
     RT_REQUIRE(q.obs_capacity >= 1, RT_EINVAL, "obs_capacity must be positive");
     RT_REQUIRE(q.hot_step_iters >= 0 && q.hot_maxit >= 0 && q.kick_terms >= 1, RT_EINVAL, "bad iteration counts");
     RT_REQUIRE((int64_t)n_sys * q.n_kick <= RT_MAX_SLOTS, RT_EINVAL, "too many (system, kick) pairs");
+    RT_REQUIRE(!q.incremental || (q.precision == RT_FP32 && !q.full_step), RT_EINVAL,
+               "the incremental form needs precision RT_FP32 and full_step = 0");
     RT_CUDA_CHECK(cudaStreamCreateWithFlags(&c->ws, cudaStreamNonBlocking));
     RT_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     RT_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
@@ -1066,6 +1161,7 @@ rt_status rt_set_density(rt_ctx* c, int32_t sys, int32_t kick, const double* h) 
           }
         o += (size_t)bi * bj;
       }
+    if (!s.ref_fresh.empty()) s.ref_fresh[kick] = 0;  // K replaced: the incremental reference is void
     RT_CUDA_CHECK(cudaMemcpyAsync(s.K[kick], buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->ws));
     reset_time(c);
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
@@ -1078,6 +1174,7 @@ rt_status rt_ground_state(rt_ctx* c, int32_t sys, int32_t order, double mu, doub
     check_sys(c, sys);
     Sys& s = *c->sys[sys];
     RT_REQUIRE(s.sinv_ready, RT_ESTATE, "call rt_inverse first");
+    std::fill(s.ref_fresh.begin(), s.ref_fresh.end(), 0);
     ground_state(c, s, order, mu, kT, e_lo, e_hi);
     reset_time(c);
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
@@ -1093,6 +1190,7 @@ rt_status rt_kick(rt_ctx* c, int32_t sys, int32_t kick, int32_t dir, double kapp
     RT_REQUIRE(std::isfinite(kappa), RT_EINVAL, "kappa must be finite");
     Sys& s = *c->sys[sys];
     RT_REQUIRE(s.sinv_ready, RT_ESTATE, "call rt_inverse first");
+    materialize(c, s);
     kick_one(c, s, kick, dir, kappa);
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
     return RT_OK;
@@ -1111,8 +1209,20 @@ rt_status rt_propagator(rt_ctx* c, double t) {
     RT_CUDA_CHECK(cudaMemcpyAsync(c->dstate, &tmp, sizeof(DevState), cudaMemcpyHostToDevice, c->ws));
     launch_begin_step(c->dstate, c->field, c->p.dt, c->n_slots, c->ws);
     for (auto& sp : c->sys) {
-      build_propagator(c, *sp);
-      sp->u_ready = true;
+      Sys& s = *sp;
+      if (incremental(c)) {
+        // the constant propagator is built in FP64 and carried as FP32 hi + lo
+        materialize(c, s);
+        build_propagator(c, s, false);
+        launch_split_u_hilo(s.U, s.dUh, s.dUl, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
+        if (s.dUHh) {
+          launch_dagger32(s.dUh, s.dUHh, s.pU->nnzb, s.B, c->ws);
+          launch_dagger32(s.dUl, s.dUHl, s.pU->nnzb, s.B, c->ws);
+        }
+      } else {
+        build_propagator(c, s, c->p.precision == RT_FP32);
+      }
+      s.u_ready = true;
     }
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
     RT_CUDA_CHECK(cudaMemcpyAsync(&tmp, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->ws));
@@ -1133,6 +1243,11 @@ rt_status rt_step(rt_ctx* c, int32_t n) {
       if (!c->p.full_step) RT_REQUIRE(sp->u_ready, RT_ESTATE, "call rt_propagator first (full_step = 0)");
     }
     if (n == 0) return RT_OK;
+    if (incremental(c)) {
+      for (auto& sp : c->sys)
+        for (int k = 0; k < c->p.n_kick; ++k)
+          if (!sp->ref_fresh[k]) make_reference(c, *sp, k);
+    }
     if (c->profiling || !c->p.use_graph) {
       for (int i = 0; i < n; ++i) enqueue_step(c);
       if (c->profiling) collect_profile(c);
@@ -1243,6 +1358,7 @@ rt_status rt_get_matrix(rt_ctx* c, int32_t sys, int32_t kick, int32_t which, dou
     Pattern* P;
     const void* v;
     bool cplx;
+    if (which == RT_MAT_K) materialize(c, s);
     matrix_by_id(c, s, kick, which, &P, &v, &cplx);
     RT_REQUIRE(vals, RT_EINVAL, "NULL output");
     int64_t need = 2 * true_elems(s, P);
@@ -1363,6 +1479,7 @@ rt_status rt_get_state(rt_ctx* c, void* buf, size_t* bytes) {
       return RT_OK;
     }
     RT_REQUIRE(*bytes >= need, RT_EINVAL, "state buffer too small");
+    for (auto& sp : c->sys) materialize(c, *sp);  // the state holds K itself
     char* o = (char*)buf;
     StateHeader h{0x52544b53544154ull, c->host_step, c->t_host, c->n_slots};
     memcpy(o, &h, sizeof(h));
@@ -1415,6 +1532,7 @@ rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
     o += sizeof(int64_t) * c->n_slots;
     for (auto& sp : c->sys) {
       Sys& s = *sp;
+      std::fill(s.ref_fresh.begin(), s.ref_fresh.end(), 0);
       for (double2* K : s.K) {
         size_t nb = sizeof(double2) * nvals(s, s.pK);
         RT_CUDA_CHECK(cudaMemcpyAsync(K, o, nb, cudaMemcpyHostToDevice, c->ws));

@@ -43,7 +43,11 @@ void launch_sum(const double* v, int64_t n, double* part, double sqrt_div, doubl
 void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const int32_t* col, const int32_t* bsize,
                    int B, const double* S, const int32_t* ks_map, const double* Dx, const double* Dy,
                    const double* Dz, const int32_t* kd_map, double* part, const DevState* st, int herm_slot,
-                   double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s);
+                   double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s,
+                   const double* ref = nullptr, double* out = nullptr);
+void launch_split_u_hilo(const double2* U, float2* hi, float2* lo, int64_t nnzb, const int32_t* rowidx,
+                         const int32_t* col, int B, cudaStream_t st);
+void launch_zaxpy(double2* z, const double2* x, const double2* y, double a, int64_t n, cudaStream_t st);
 int launch_unitarity_dev(const double2* E, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
                          const int32_t* bsize, int B, const double* S, const int32_t* us_map, double* part_max,
                          double* part_sum, cudaStream_t st);

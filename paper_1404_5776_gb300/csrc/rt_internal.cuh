@@ -147,6 +147,9 @@ struct GemmArgs {
   const void* addend;
   const int32_t* add_map;   // P_K block -> addend block
   unsigned long long* herm_max;  // max |K_ii - K_ii^dagger| bits
+  const void* base2;        // incremental form: FP64 R at the output block (dense blocks) or null
+  const void* addend2;      // incremental form: FP32 N_lo at the output block (FP32 block layout) or null
+  const void* addend3;      // incremental form: FP32 M_lo through add_map (FP32 block layout) or null
   const void* zero;         // a zero block (FP32 kernels stage it for missing triples)
   int* err;                 // device error word (bounded waits that gave up)
 };

@@ -208,26 +208,41 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
     acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, 16);
   }
   const int q = g.item_blk[item];
-  if constexpr (EPI == EPI_STORE) {
+  if constexpr (EPI == EPI_STORE || EPI == EPI_ADD) {
     float2* __restrict__ C = static_cast<float2*>(g.C);
     if (h == 0 && c < BS) {
+      if constexpr (EPI == EPI_ADD) {  // C += acc (all loads first)
+        float2 old[BS];
+#pragma unroll
+        for (int r = 0; r < BS; ++r) old[r] = C[(int64_t)q * SB + r * RS + c];
+#pragma unroll
+        for (int r = 0; r < BS; ++r) acc[r] = make_float2(old[r].x + acc[r].x, old[r].y + acc[r].y);
+      }
 #pragma unroll
       for (int r = 0; r < BS; ++r) C[(int64_t)q * SB + r * RS + c] = acc[r];
     }
     // delta form: also W = K + M in FP32 (K in FP64, dense blocks, through
-    // the map from this pattern to K's; -1 = no K block)
+    // the map from this pattern to K's; -1 = no K block).  In the incremental
+    // form this is the lo-part product and g.addend holds the hi part:
+    // W = dK + (M_hi + M_lo), summed in FP64.
     if (g.base) {
       const double2* __restrict__ Kb = static_cast<const double2*>(g.base);
+      const float2* __restrict__ Mh = static_cast<const float2*>(g.addend);
       float2* __restrict__ W = static_cast<float2*>(g.U);
       const int kq = g.add_map ? g.add_map[q] : q;
       if (h == 0 && c < BS) {
         double2 kv[BS];
+        float2 mh[BS];
 #pragma unroll
-        for (int r = 0; r < BS; ++r) kv[r] = (kq >= 0) ? Kb[(int64_t)kq * NE + r * BS + c] : make_double2(0.0, 0.0);
+        for (int r = 0; r < BS; ++r) {
+          kv[r] = (kq >= 0) ? Kb[(int64_t)kq * NE + r * BS + c] : make_double2(0.0, 0.0);
+          mh[r] = Mh ? Mh[(int64_t)q * SB + r * RS + c] : make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int r = 0; r < BS; ++r)
           W[(int64_t)q * SB + r * RS + c] =
-              make_float2((float)((double)acc[r].x + kv[r].x), (float)((double)acc[r].y + kv[r].y));
+              make_float2((float)(((double)mh[r].x + (double)acc[r].x) + kv[r].x),
+                          (float)(((double)mh[r].y + (double)acc[r].y) + kv[r].y));
       }
     }
   } else if constexpr (EPI == EPI_DELTA_SANDWICH) {
@@ -246,6 +261,22 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
       for (int r = 0; r < BS; ++r) {
         val[r] = base[(int64_t)q * NE + r * BS + c];
         mv[r] = (aq >= 0) ? add[(int64_t)aq * SB + r * RS + c] : make_float2(0.f, 0.f);
+      }
+      if (g.base2) {
+        // incremental form: dK' = dK + R + M_hi + M_lo + N_lo + N_hi, every
+        // part added in FP64 (the lo parts are below FP32 resolution of the hi)
+        const double2* __restrict__ R = static_cast<const double2*>(g.base2);
+        const float2* __restrict__ Nl = static_cast<const float2*>(g.addend2);
+        const float2* __restrict__ Ml = static_cast<const float2*>(g.addend3);
+#pragma unroll
+        for (int r = 0; r < BS; ++r) {
+          double2 rv = R[(int64_t)q * NE + r * BS + c];
+          float2 nl = Nl[(int64_t)q * SB + r * RS + c];
+          float2 ml = (aq >= 0) ? Ml[(int64_t)aq * SB + r * RS + c] : make_float2(0.f, 0.f);
+          val[r] = make_double2(val[r].x + rv.x + (((double)nl.x + (double)ml.x) + (double)acc[r].x),
+                                val[r].y + rv.y + (((double)nl.y + (double)ml.y) + (double)acc[r].y));
+          acc[r] = make_float2(0.f, 0.f);
+        }
       }
 #pragma unroll
       for (int r = 0; r < BS; ++r)
@@ -462,12 +493,14 @@ bool launch_gemm13_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const Ge
   if (!attr_done) {
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_DELTA_SANDWICH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_r32<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_r32<EPI_STORE_ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
     attr_done = true;
   }
   if (cplx) {
     if (epi == EPI_STORE) k_gemm13_c32<EPI_STORE><<<(unsigned)grid, WARPS * 32, smem_c, st>>>(g);
+    else if (epi == EPI_ADD) k_gemm13_c32<EPI_ADD><<<(unsigned)grid, WARPS * 32, smem_c, st>>>(g);
     else if (epi == EPI_DELTA_SANDWICH) k_gemm13_c32<EPI_DELTA_SANDWICH><<<(unsigned)grid, WARPS * 32, smem_c, st>>>(g);
     else return false;
   } else {
