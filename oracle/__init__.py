@@ -20,6 +20,11 @@ The oracle follows O'Rourke & Bowler (arXiv:1404.5776) step by step:
 * Crank-Nicolson form U = (S + i dt/2 H)^-1 (S - i dt/2 H), with the inverse
   by the same Hotelling iteration warm-started from the previous step (an
   added propagator mode; the paper uses EM throughout).
+* Sec. II.A also defines the enforced-time-reversal-symmetry propagator
+  U_ETRS = exp(-i dt/2 S^-1 H(t+dt)) exp(-i dt/2 S^-1 H(t)) and the fourth-order
+  Magnus propagator U_M4 = exp(M), M = -i dt/2 [T(t1) + T(t2)]
+  - (sqrt(3) dt^2 / 12) [T(t2), T(t1)], t_{2,1} = t + (1/2 +- sqrt(3)/6) dt,
+  T = S^-1 H; every exponential by the same truncated Taylor series.
 
 Two modes share these definitions: the truncated block-sparse mode here (C
 kernels in ``oracle.c`` for patterns and products) and the dense mode in
@@ -518,12 +523,39 @@ class Propagator:
         T0 = spgemm(self.Sinv, self.H0, self.pats["T"])
         self.K = fermi_operator_expansion(T0, self.Sinv, self.pats["K"], order, mu, kT, e_lo, e_hi, jackson)
 
+    def _T(self, t):
+        """T(t) = cut_{r_T}(S^-1 H(t))."""
+        H = hamiltonian(self.H0, self.D[self.p.field_dir], field_value(self.p.field, t))
+        return spgemm(self.Sinv, H, self.pats["T"])
+
     def propagator(self, t):
-        """U for [t, t+dt] with H at the midpoint t + dt/2 (eq. EM)."""
+        """U for [t, t+dt]: eq. EM (H at the midpoint t + dt/2), the CN form,
+        ETRS or the fourth-order Magnus form (Sec. II.A)."""
         p = self.p
         E = field_value(p.field, t + 0.5 * p.dt)
         Hm = hamiltonian(self.H0, self.D[p.field_dir], E)
         info = {"iters": 0, "resid": 0.0}
+        if p.prop == "etrs":
+            Ua, _ = taylor_em(self._T(t), 0.5 * p.dt, p.taylor_terms, self.pats["U"])
+            Ub, _ = taylor_em(self._T(t + p.dt), 0.5 * p.dt, p.taylor_terms, self.pats["U"])
+            self.U = spgemm(Ub, Ua, self.pats["U"])
+            return self.U, info
+        if p.prop == "m4":
+            r3 = math.sqrt(3.0)
+            T1 = self._T(t + (0.5 - r3 / 6.0) * p.dt)
+            T2 = self._T(t + (0.5 + r3 / 6.0) * p.dt)
+            pu = self.pats["U"]
+            comm = axpy(-1.0, spgemm(T1, T2, pu), spgemm(T2, T1, pu))  # [T2, T1]
+            Msum = axpy(1.0, restrict(T1, pu), restrict(T2, pu))
+            Om = BlockMatrix(T1.bsize, pu, -0.5j * p.dt * Msum.val - (r3 * p.dt * p.dt / 12.0) * comm.val, Msum.voff)
+            U = identity(T1.bsize, pu)
+            P = Om
+            for n in range(1, p.taylor_terms):
+                if n > 1:
+                    P = spgemm(Om, P, pu)
+                U = axpy(1.0 / math.factorial(n), P, U)
+            self.U = U
+            return U, info
         if p.prop == "em":
             T = spgemm(self.Sinv, Hm, self.pats["T"])
             U, _ = taylor_em(T, p.dt, p.taylor_terms, self.pats["U"])
