@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--radius", type=float, default=8.0)
     ap.add_argument("--ncell", type=int, default=8)
     ap.add_argument("--basis", default="spd13")
-    ap.add_argument("--prop", default="em", choices=["em", "cn"])
+    ap.add_argument("--prop", default="em", choices=["em", "cn", "etrs", "m4"])
     ap.add_argument("--foe-order", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
@@ -174,6 +174,20 @@ def alu_peaks(torch):
 # ----------------------------------------------------------------------------
 # ranks (one process per GPU, independent replicas; no data-path collective)
 # ----------------------------------------------------------------------------
+def nvtx_push(torch, name):
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except Exception:  # NVTX markers are optional
+        pass
+
+
+def nvtx_pop(torch):
+    try:
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
     """The slowest rank's value (timings are reported as the max over ranks)."""
     if dist is None:
@@ -241,7 +255,7 @@ def run_gpu(args):
     n64 = args.fp64_steps if args.fp64_steps is not None else args.steps
     res = {}
 
-    def timed(ctx, nsteps, warm):
+    def timed(ctx, nsteps, warm, label):
         ctx.step(warm)
         ctx.synchronize()
         if dist:
@@ -250,7 +264,10 @@ def run_gpu(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record()
+        # an NVTX range marks the timed launches (ncu --nvtx-include "timed_<label>/")
+        nvtx_push(torch, "timed_" + label)
         ctx.step(nsteps)
+        nvtx_pop(torch)
         ev1.record()
         torch.cuda.synchronize()
         ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
@@ -259,10 +276,10 @@ def run_gpu(args):
     clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_r{rank}.csv")
     clocks.start()
-    ms64 = timed(c64, n64, args.warmup)
-    ms32 = timed(c32, args.steps, args.warmup)
-    ms64p = timed(c64p, n64, args.warmup)
-    ms32i = timed(c32i, args.steps, args.warmup) if c32i else float("nan")
+    ms64 = timed(c64, n64, args.warmup, "fp64")
+    ms32 = timed(c32, args.steps, args.warmup, "fp32_mixed")
+    ms64p = timed(c64p, n64, args.warmup, "fp64_propagation")
+    ms32i = timed(c32i, args.steps, args.warmup, "fp32_incremental") if c32i else float("nan")
     clk = clocks.stop()
 
     flops64, bytes64 = c64.step_work()
@@ -387,6 +404,7 @@ def run_gpu(args):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
         "device": dev_name,
+        "device_mem_gb": round(torch.cuda.max_memory_allocated() / 1e9, 2),
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, s, budget_s=20.0)

@@ -16,6 +16,11 @@
  * An added propagator mode uses the Crank-Nicolson form
  *   U = (S + i dt/2 H)^-1 (S - i dt/2 H)
  * with the inverse by Hotelling's iteration warm-started from the previous step.
+ * The paper's other two propagators (Sec. II.A) are available as well:
+ *   U_ETRS = exp(-i dt/2 T(t+dt)) exp(-i dt/2 T(t)),  T = S^-1 H
+ *   U_M4   = exp(-i dt/2 [T(t1) + T(t2)] - sqrt(3) dt^2/12 [T(t2), T(t1)]),
+ *            t_{2,1} = t + (1/2 +- sqrt(3)/6) dt
+ * every exponential by the same truncated Taylor series.
  *
  * Conventions of every entry point:
  *   - Pointers named h_* or documented "host" are host memory; the library
@@ -67,7 +72,7 @@ typedef enum {
   RT_ESTATE = 8      /* call not valid in the context's current state    */
 } rt_status;
 
-enum { RT_PROP_EM = 0, RT_PROP_CN = 1 };
+enum { RT_PROP_EM = 0, RT_PROP_CN = 1, RT_PROP_ETRS = 2, RT_PROP_M4 = 3 };
 enum { RT_FP64 = 0, RT_FP32 = 1 };
 enum { RT_FIELD_NONE = 0, RT_FIELD_GAUSSIAN = 1, RT_FIELD_CONSTANT = 2 };
 
@@ -122,7 +127,9 @@ typedef struct {
 typedef struct {
   double r_Sinv, r_T, r_U, r_K, r_M; /* truncation radii (Angstrom)                 */
   double dt;                /* time step (a.u.)                                   */
-  int32_t prop;             /* RT_PROP_EM (paper) or RT_PROP_CN                    */
+  int32_t prop;             /* RT_PROP_EM (paper, default), RT_PROP_CN, RT_PROP_ETRS
+                               or RT_PROP_M4 (both Sec. II.A); ETRS and M4 build
+                               U in FP64 in either precision                      */
   int32_t taylor_terms;     /* EM: terms of the exponential series in total (6)  */
   double hot_tol;           /* Hotelling tolerance on ||I - S X||_F / sqrt(n)     */
   int32_t hot_maxit;        /* Hotelling iteration cap for rt_inverse             */

@@ -25,7 +25,7 @@ from . import _build
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ENUMERIC, RT_ETIMEOUT, RT_EINTERNAL, RT_ESTATE = range(9)
 STATUS_NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV", 5: "RT_ENUMERIC",
                 6: "RT_ETIMEOUT", 7: "RT_EINTERNAL", 8: "RT_ESTATE"}
-RT_PROP_EM, RT_PROP_CN = 0, 1
+RT_PROP_EM, RT_PROP_CN, RT_PROP_ETRS, RT_PROP_M4 = 0, 1, 2, 3
 RT_FP64, RT_FP32 = 0, 1
 RT_FIELD_NONE, RT_FIELD_GAUSSIAN, RT_FIELD_CONSTANT = 0, 1, 2
 RT_MAT_S, RT_MAT_H0, RT_MAT_DX, RT_MAT_DY, RT_MAT_DZ, RT_MAT_SINV, RT_MAT_T, RT_MAT_U, RT_MAT_K, RT_MAT_X = range(10)
@@ -220,7 +220,7 @@ def make_params(**kw) -> rt_params:
     p = rt_default_params()
     for k, v in kw.items():
         if k == "prop" and isinstance(v, str):
-            v = {"em": RT_PROP_EM, "cn": RT_PROP_CN}[v]
+            v = {"em": RT_PROP_EM, "cn": RT_PROP_CN, "etrs": RT_PROP_ETRS, "m4": RT_PROP_M4}[v]
         if k == "precision" and isinstance(v, str):
             v = {"fp64": RT_FP64, "fp32": RT_FP32}[v]
         setattr(p, k, v)

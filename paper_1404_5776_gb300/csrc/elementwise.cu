@@ -21,7 +21,12 @@ __device__ __forceinline__ double field_at(const FieldParams& f, double t) {
 }
 
 __global__ void k_begin_step(DevState* s, FieldParams f, double dt, int n_herm) {
-  s->E_mid = field_at(f, s->t + 0.5 * dt);
+  const double t = s->t, r3 = sqrt(3.0);
+  s->E[0] = field_at(f, t + 0.5 * dt);
+  s->E[1] = field_at(f, t);
+  s->E[2] = field_at(f, t + dt);
+  s->E[3] = field_at(f, t + (0.5 - r3 / 6.0) * dt);
+  s->E[4] = field_at(f, t + (0.5 + r3 / 6.0) * dt);
   for (int i = 0; i < n_herm; ++i) s->herm_bits[i] = 0ull;
 }
 
@@ -43,18 +48,46 @@ void launch_end_step(DevState* s, double dt, cudaStream_t st) {
 // H(t+dt/2) = H0 - E D_j
 // ---------------------------------------------------------------------------
 __global__ void k_field_axpy(const double* __restrict__ H0, const double* __restrict__ D, const DevState* s,
-                             double scale, double* __restrict__ Hm, int64_t n) {
+                             int which, double scale, double* __restrict__ Hm, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double E = s ? s->E_mid * scale : scale;
+  double E = s ? s->E[which] * scale : scale;
   for (; i < n; i += (int64_t)gridDim.x * blockDim.x) Hm[i] = H0[i] - E * D[i];
 }
 
-void launch_field_axpy(const double* H0, const double* D, const DevState* s, double scale, double* Hm, int64_t n,
-                       cudaStream_t st) {
+void launch_field_axpy(const double* H0, const double* D, const DevState* s, int which, double scale, double* Hm,
+                       int64_t n, cudaStream_t st) {
   if (n == 0) return;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  k_field_axpy<<<(unsigned)g, 256, 0, st>>>(H0, D, s, scale, Hm, n);
+  k_field_axpy<<<(unsigned)g, 256, 0, st>>>(H0, D, s, which, scale, Hm, n);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// M4 exponent (Sec. II.A) on P_U: Om = -i dt/2 (T1 + T2) - (sqrt(3) dt^2/12) [T2, T1]
+// with [T2, T1] = C21 - C12 (both cut to P_U); T1, T2 on P_T through u_to_t.
+__global__ void k_m4_omega(const double* __restrict__ T1, const double* __restrict__ T2,
+                           const int32_t* __restrict__ u_to_t, const double* __restrict__ C21,
+                           const double* __restrict__ C12, double dt, double2* __restrict__ Om, int64_t nnzb_u,
+                           int NE) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double cc = sqrt(3.0) * dt * dt / 12.0;
+  for (; idx < nnzb_u * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int tq = u_to_t ? u_to_t[q] : (int)q;
+    double ts = 0.0;
+    if (tq >= 0) ts = T1[(int64_t)tq * NE + e] + T2[(int64_t)tq * NE + e];
+    Om[idx] = make_double2(-cc * (C21[idx] - C12[idx]), -0.5 * dt * ts);
+  }
+}
+
+void launch_m4_omega(const double* T1, const double* T2, const int32_t* u_to_t, const double* C21, const double* C12,
+                     double dt, double2* Om, int64_t nnzb_u, int B, cudaStream_t st) {
+  int64_t n = nnzb_u * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_m4_omega<<<(unsigned)g, 256, 0, st>>>(T1, T2, u_to_t, C21, C12, dt, Om, nnzb_u, B * B);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -4,6 +4,9 @@
 //   EM:  H(t+dt/2) = H0 - E D_j;  T = cut_{r_T}(S^-1 H);  T^n = cut_{r_U}(T T^{n-1});
 //        U = sum_{n<6} (-i dt)^n T^n / n!
 //   CN:  A = S + i dt/2 H, X <- X(2I - A X) (warm start), U = cut_{r_U}(X (S - i dt/2 H))
+//   ETRS: U = cut_{r_U}(exp(-i dt/2 T(t+dt)) exp(-i dt/2 T(t)))
+//   M4:  Om = -i dt/2 (T1 + T2) - sqrt(3) dt^2/12 [T2, T1] at the Gauss-Legendre
+//        times t1, t2;  U = sum_{n<6} Om^n / n!  (powers cut to r_U)
 //   M = cut_{r_M}(U K);  K' = M U^dagger on the upper blocks of P_K, mirrored;
 //   Tr(K S), Tr(K D_xyz) recorded per step.
 // All work runs on an internal stream ordered against the caller's stream with
@@ -63,7 +66,7 @@ struct Sys {
   // FP64 values (padded blocks)
   double *S = nullptr, *H0 = nullptr, *D[3] = {nullptr, nullptr, nullptr}, *Hm = nullptr;
   double *Sinv = nullptr, *Zs = nullptr, *Xs2 = nullptr;
-  double *T = nullptr, *P0 = nullptr, *P1 = nullptr, *T0 = nullptr, *TD = nullptr;
+  double *T = nullptr, *P0 = nullptr, *P1 = nullptr, *T0 = nullptr, *TD = nullptr, *T2 = nullptr;
   double2 *U = nullptr, *M = nullptr;
   std::vector<double2*> K;
   double2 *Acn = nullptr, *Bcn = nullptr, *X = nullptr, *Xn = nullptr, *Zc = nullptr;
@@ -415,10 +418,21 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
   triples_for(c, s, s.pSinv, false, s.pH, false, s.pT, false);      // T = S^-1 H
   triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);         // M = U K
   triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);           // K' = M U^dagger
-  if (p.prop == RT_PROP_EM) {
-    triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);  // T^2
+  if (p.prop != RT_PROP_CN) {
+    triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);  // T^2 (M4: T1 T2, T2 T1)
     triples_for(c, s, s.pT, false, s.pU, false, s.pU, false);  // T^n
-  } else {
+  }
+  if (p.prop == RT_PROP_ETRS || p.prop == RT_PROP_M4) {
+    // ETRS: the two half-step exponentials; M4: Om and two power buffers
+    s.X = c->arena.get_n<double2>(nvals(s, s.pU));
+    s.Xn = c->arena.get_n<double2>(nvals(s, s.pU));
+    triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);  // complex products on P_U
+    if (p.prop == RT_PROP_M4) {
+      s.Zc = c->arena.get_n<double2>(nvals(s, s.pU));
+      s.T2 = c->arena.get_n<double>(nvals(s, s.pT));
+    }
+  }
+  if (p.prop == RT_PROP_CN) {
     s.a_to_s = block_map(c, s.pA, s.pS, false);
     s.a_to_h = block_map(c, s.pA, s.pH, false);
     s.Acn = c->arena.get_n<double2>(nvals(s, s.pA));
@@ -562,8 +576,10 @@ static void taylor_coef(int n, double dt, double* mag, int* imag) {
 }
 
 // U = sum_{n<terms} c_n T^n with T real on P_T, powers cut to P_U.  FP64 U
-// (ident) or the FP32 difference dU = U - I.
-static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int terms, bool fp32_delta) {
+// (into Uout, default s.U) or the FP32 difference dU = U - I.
+static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int terms, bool fp32_delta,
+                          double2* Uout = nullptr) {
+  if (!Uout) Uout = s.U;
   TripleInfo& t2 = triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);
   TripleInfo& tn = triples_for(c, s, s.pT, false, s.pU, false, s.pU, false);
   double c1 = 0.0;
@@ -571,7 +587,7 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
   taylor_coef(1, dt, &c1, &c1i);
   if (!fp32_delta) {
     run(c, PC_MISC, 0, 0, [&] {
-      launch_taylor_init(s.U, false, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
+      launch_taylor_init(Uout, false, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
                          terms > 1 ? c1 : 0.0, c1i, 1, c->ws);
     });
     const double* prev = T;
@@ -581,7 +597,7 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
       int ci;
       taylor_coef(n, dt, &cn, &ci);
       GemmArgs g = args(T, prev, bufs[n % 2]);
-      g.U = s.U;
+      g.U = Uout;
       g.coef = cn;
       g.coef_imag = ci;
       gemm(c, s, PC_TAYLOR, n == 2 ? t2 : tn, false, false, false, false, EPI_STORE_ACC, g, s.pU);
@@ -618,25 +634,87 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
   }
 }
 
+// field samples of the device step state (k_begin_step)
+enum { E_MID = 0, E_T = 1, E_TDT = 2, E_T1 = 3, E_T2 = 4 };
+
+// H = H0 - E(t_which) D_j into s.Hm
+static void field_hamiltonian(rt_ctx* c, Sys& s, int which) {
+  const int dir = c->field.dir;
+  run(c, PC_FIELD, 0, 24.0 * nvals(s, s.pH),
+      [&] { launch_field_axpy(s.H0, s.D[dir], c->dstate, which, 1.0, s.Hm, (int64_t)nvals(s, s.pH), c->ws); });
+}
+
+// T = cut_{r_T}(S^-1 H(t_which)) into Tout
+static void field_T(rt_ctx* c, Sys& s, int which, double* Tout) {
+  field_hamiltonian(c, s, which);
+  TripleInfo& tT = triples_for(c, s, s.pSinv, false, s.pH, false, s.pT, false);
+  gemm(c, s, PC_T, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.Hm, Tout), s.pT);
+}
+
+// ETRS (Sec. II.A): U = cut(exp(-i dt/2 T(t+dt)) exp(-i dt/2 T(t))), each
+// exponential by the truncated Taylor series
+static void build_etrs(rt_ctx* c, Sys& s) {
+  const rt_params& p = c->p;
+  field_T(c, s, E_T, s.T);
+  taylor_series(c, s, s.T, 0.5 * p.dt, p.taylor_terms, false, s.X);
+  field_T(c, s, E_TDT, s.T);
+  taylor_series(c, s, s.T, 0.5 * p.dt, p.taylor_terms, false, s.Xn);
+  TripleInfo& tUU = triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);
+  gemm(c, s, PC_TAYLOR, tUU, false, true, false, false, EPI_STORE, args(s.Xn, s.X, s.U), s.pU);
+}
+
+// fourth-order Magnus (Sec. II.A): T1, T2 at t + (1/2 -+ sqrt(3)/6) dt,
+// Om = -i dt/2 (T1 + T2) - sqrt(3) dt^2/12 [T2, T1] on P_U,
+// U = sum_{n<terms} Om^n / n! with Om^n = cut(Om Om^{n-1})
+static void build_m4(rt_ctx* c, Sys& s) {
+  const rt_params& p = c->p;
+  field_T(c, s, E_T1, s.T);
+  field_T(c, s, E_T2, s.T2);
+  TripleInfo& tTT = triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);
+  gemm(c, s, PC_TAYLOR, tTT, false, false, false, false, EPI_STORE, args(s.T2, s.T, s.P0), s.pU);  // T2 T1
+  gemm(c, s, PC_TAYLOR, tTT, false, false, false, false, EPI_STORE, args(s.T, s.T2, s.P1), s.pU);  // T1 T2
+  const int64_t nu = (int64_t)nvals(s, s.pU);
+  run(
+      c, PC_MISC, 0, 0,
+      [&] {
+        launch_m4_omega(s.T, s.T2, s.u_to_t, s.P0, s.P1, p.dt, s.Zc, s.pU->nnzb, s.B, c->ws);
+        launch_identity((double*)s.U, true, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, 1.0, c->ws);
+        if (p.taylor_terms > 1) launch_zaxpy(s.U, s.U, s.Zc, 1.0, nu, c->ws);
+      },
+      p.taylor_terms > 1 ? 3 : 2);
+  TripleInfo& tUU = triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);
+  const double2* prev = s.Zc;
+  double2* bufs[2] = {s.X, s.Xn};
+  double inv_fact = 1.0;
+  for (int n = 2; n < p.taylor_terms; ++n) {
+    inv_fact /= n;
+    double2* out = bufs[n % 2];
+    gemm(c, s, PC_TAYLOR, tUU, false, true, false, false, EPI_STORE, args(s.Zc, prev, out), s.pU);
+    run(c, PC_MISC, 0, 0, [&] { launch_zaxpy(s.U, s.U, out, inv_fact, nu, c->ws); });
+    prev = out;
+  }
+}
+
 static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
   const rt_params& p = c->p;
-  const int dir = c->field.dir;
   if (p.prop == RT_PROP_EM) {
     if (fp32) {
       // T(t+dt/2) = T0 - E T_D (linearity of the cut product in E)
       run(c, PC_FIELD, 0, 16.0 * nvals(s, s.pT),
-          [&] { launch_field_axpy(s.T0, s.TD, c->dstate, 1.0, s.T, (int64_t)nvals(s, s.pT), c->ws); });
+          [&] { launch_field_axpy(s.T0, s.TD, c->dstate, E_MID, 1.0, s.T, (int64_t)nvals(s, s.pT), c->ws); });
       taylor_series(c, s, s.T, p.dt, p.taylor_terms, true);
     } else {
-      run(c, PC_FIELD, 0, 24.0 * nvals(s, s.pH),
-          [&] { launch_field_axpy(s.H0, s.D[dir], c->dstate, 1.0, s.Hm, (int64_t)nvals(s, s.pH), c->ws); });
-      TripleInfo& tT = triples_for(c, s, s.pSinv, false, s.pH, false, s.pT, false);
-      gemm(c, s, PC_T, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.Hm, s.T), s.pT);
+      field_T(c, s, E_MID, s.T);
       taylor_series(c, s, s.T, p.dt, p.taylor_terms, false);
     }
+    return;
+  }
+  if (p.prop == RT_PROP_ETRS) {
+    build_etrs(c, s);
+  } else if (p.prop == RT_PROP_M4) {
+    build_m4(c, s);
   } else {
-    run(c, PC_FIELD, 0, 24.0 * nvals(s, s.pH),
-        [&] { launch_field_axpy(s.H0, s.D[dir], c->dstate, 1.0, s.Hm, (int64_t)nvals(s, s.pH), c->ws); });
+    field_hamiltonian(c, s, E_MID);
     run(c, PC_FIELD, 0, 48.0 * nvals(s, s.pA), [&] {
       launch_cn_operands(s.S, s.a_to_s, s.Hm, s.a_to_h, 0.5 * p.dt, s.Acn, s.Bcn, s.pA->nnzb, s.B, c->ws);
     });
@@ -661,12 +739,12 @@ static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
       });
     if (p.hot_step_iters > 0) run(c, PC_MISC, 0, 0, [&] { launch_set_hot(c->dstate, s.scal + 1, p.hot_step_iters, c->ws); });
     gemm(c, s, PC_CN_U, tXB, false, true, false, false, EPI_STORE, args(s.X, s.Bcn, s.U), s.pU);
-    if (fp32) {
-      // dU = U - I in FP32 for the delta-form sandwich
-      run(c, PC_MISC, 0, 0,
-          [&] { launch_u_minus_i_f32(s.U, s.dUf, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws); });
-      if (s.dUH) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
-    }
+  }
+  if (fp32) {
+    // FP64 U; dU = U - I in FP32 for the delta-form sandwich
+    run(c, PC_MISC, 0, 0,
+        [&] { launch_u_minus_i_f32(s.U, s.dUf, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws); });
+    if (s.dUH) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
   }
 }
 
@@ -1046,7 +1124,8 @@ rt_status rt_create(rt_ctx** out, const rt_system* sys, int32_t n_sys, const rt_
     const rt_params& q = c->p;
     RT_REQUIRE(q.r_Sinv > 0 && q.r_T > 0 && q.r_U > 0 && q.r_K > 0 && q.r_M > 0, RT_EINVAL, "radii must be positive");
     RT_REQUIRE(q.dt > 0 && std::isfinite(q.dt), RT_EINVAL, "dt must be positive");
-    RT_REQUIRE(q.prop == RT_PROP_EM || q.prop == RT_PROP_CN, RT_EINVAL, "prop must be RT_PROP_EM or RT_PROP_CN");
+    RT_REQUIRE(q.prop >= RT_PROP_EM && q.prop <= RT_PROP_M4, RT_EINVAL,
+               "prop must be RT_PROP_EM, RT_PROP_CN, RT_PROP_ETRS or RT_PROP_M4");
     RT_REQUIRE(q.taylor_terms >= 1 && q.taylor_terms <= 32, RT_EINVAL, "taylor_terms must be in 1..32");
     RT_REQUIRE(q.precision == RT_FP64 || q.precision == RT_FP32, RT_EINVAL, "precision must be RT_FP64 or RT_FP32");
     RT_REQUIRE(q.n_kick >= 1 && q.n_kick <= 3, RT_EINVAL, "n_kick must be in 1..3");

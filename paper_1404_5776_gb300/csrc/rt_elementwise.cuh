@@ -17,7 +17,7 @@ constexpr int RT_MAX_SLOTS = 256;  // (system, kick) pairs
 struct DevState {
   int64_t step;
   double t;
-  double E_mid;
+  double E[5];  // field at t + dt/2, t, t + dt, t1, t2 (Gauss-Legendre points of M4)
   double hot_resid;
   int hot_iters;
   int pad;
@@ -26,8 +26,12 @@ struct DevState {
 
 void launch_begin_step(DevState* s, const FieldParams& f, double dt, int n_herm, cudaStream_t st);
 void launch_end_step(DevState* s, double dt, cudaStream_t st);
-void launch_field_axpy(const double* H0, const double* D, const DevState* s, double scale, double* Hm, int64_t n,
-                       cudaStream_t st);
+// Hm = H0 - s->E[which] * D (s == nullptr: Hm = H0 - scale * D)
+void launch_field_axpy(const double* H0, const double* D, const DevState* s, int which, double scale, double* Hm,
+                       int64_t n, cudaStream_t st);
+// M4 exponent on P_U: Om = -i dt/2 (T1 + T2) - (sqrt(3) dt^2 / 12) (C21 - C12)
+void launch_m4_omega(const double* T1, const double* T2, const int32_t* u_to_t, const double* C21, const double* C12,
+                     double dt, double2* Om, int64_t nnzb_u, int B, cudaStream_t st);
 void launch_taylor_init(void* U, bool fp32, int64_t nnzb_u, const int32_t* u_rowidx, const int32_t* u_col,
                         const void* T, bool t_fp32, const int32_t* u_to_t, int B, double c1, int c1_imag, int ident,
                         cudaStream_t st);

@@ -49,7 +49,7 @@ def _pair(rt, basis, prop, steps, r=6.0):
 
 
 @pytest.mark.parametrize("basis", ["spd13", "sp4"])
-@pytest.mark.parametrize("prop", ["em", "cn"])
+@pytest.mark.parametrize("prop", ["em", "cn", "etrs", "m4"])
 def test_mixed_dipole_and_density(rt, basis, prop):
     ctx, obs, Kg, rows, ref = _pair(rt, basis, prop, 40)
     ctx.close()

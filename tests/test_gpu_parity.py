@@ -146,6 +146,35 @@ def test_step_parity_gaussian_pulse_and_no_graph(rt):
         assert relerr(obs[:, col], rows[:, col]) < REL
 
 
+@pytest.mark.parametrize("prop", ["etrs", "m4"])
+@pytest.mark.parametrize("basis,radii", [("sp4", dict(r_Sinv=6.0, r_T=6.0, r_U=7.0, r_K=6.0, r_M=7.0)),
+                                         ("spd13", dict(r_Sinv=6.0, r_T=7.0, r_U=6.0, r_K=6.0, r_M=6.0))])
+def test_etrs_m4_parity_under_pulse(rt, prop, basis, radii):
+    """ETRS and fourth-order Magnus (Sec. II.A) under a Gaussian pulse, so that
+    T(t), T(t+dt) and the Gauss-Legendre samples T(t1), T(t2) all differ; with
+    r_T > r_U the exponent is cut to P_U, with r_T < r_U it is zero-extended."""
+    s = synth.diamond_system(2, basis, 6.0, 6.0)
+    field = dict(kind=rt.RT_FIELD_GAUSSIAN, dir=2, E0=5e-3, t0=0.15, sigma=0.1, omega=1.3)
+    obs, Kg, Ug, rows, ref = _run_pair(rt, s, prop, radii, 8, 2 * s.n_atoms, field=field)
+    assert relerr(Kg, ref.K.val) < REL
+    assert relerr(Ug, ref.U.val) < REL
+    for col in (1, 3, 5, 7):
+        assert relerr(obs[:, col], rows[:, col]) < REL, col
+    ind_g = obs[:, 7] - obs[0, 7]
+    ind_r = rows[:, 7] - rows[0, 7]
+    assert np.abs(ind_g - ind_r).max() <= 1e-7 * np.abs(ind_r).max()
+
+
+@pytest.mark.parametrize("prop", ["etrs", "m4"])
+def test_etrs_m4_propagation_step(rt, prop):
+    """Propagation step (U built once at t = 0, reused) for both propagators."""
+    s = synth.diamond_system(2, "sp4", 6.0, 6.0)
+    field = dict(kind=rt.RT_FIELD_CONSTANT, dir=0, E0=1e-3)
+    obs, Kg, _, rows, ref = _run_pair(rt, s, prop, _radii(6.0), 6, s.n // 2, field=field, full_step=0)
+    assert relerr(Kg, ref.K.val) < REL
+    assert relerr(obs[:, 3], rows[:, 3]) < REL
+
+
 def test_propagation_step_reuses_u(rt):
     s = synth.diamond_system(2, "sp4", 6.0, 6.0)
     obs, Kg, _, rows, ref = _run_pair(rt, s, "em", _radii(6.0), 8, s.n // 2, full_step=0)
