@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--foe-order", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
+    ap.add_argument("--study", default=None, choices=["truncation"],
+                    help="run a study instead of the benchmark and print its JSON line")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NSTEPS",
                     help="instead of timing: run both paths NSTEPS steps and report their agreement")
     return ap.parse_args()
@@ -140,6 +142,21 @@ def measured_peaks():
         except Exception:
             p = {}
     return p
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel from an ncu capture of
+# the same kernel and workload, keyed by (path, kernel class); None when the kernel
+# changed after the capture.
+TRAFFIC = {}
+
+
+def derived_alu_peaks(torch, sm_max_mhz):
+    """ALU peaks from unit counts and the maximum SM clock, TFLOP/s: FP32 is
+    128 FMA lanes per SM x 2 flops; FP64 is GB300's nominal 1.25 TFLOP/s at
+    2070 MHz scaled to the clock (2 FP64 FMA per clock per SM on 152 SMs)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ghz = (sm_max_mhz or 2070.0) / 1e3
+    return {"fp32": sms * 128 * 2 * ghz / 1e3, "fp64": sms * 2 * 2 * ghz / 1e3, "sms": sms, "sm_max_ghz": ghz}
 
 
 def alu_peaks(torch):
@@ -339,14 +356,17 @@ def run_gpu(args):
     per_launch_flops = d["flops"] / max(d["launches"], 1)
     per_launch_ms = d["ms"] / max(d["launches"], 1)
     peaks = alu_peaks(torch) if rank == 0 else {}
+    derived = derived_alu_peaks(torch, clk.get("sm_max_mhz") if isinstance(clk, dict) else None)
     mp = measured_peaks()
     if d["flops"] > 0:
         achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12
-        peak = peaks.get(hp)
-        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3) if peak else None,
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None, "traffic": None,
-                "peak_source": f"measured: cuBLAS {'SGEMM (TF32 off)' if hp == 'fp32' else 'DGEMM'} 2n^3/t on this GPU",
-                "measured_peaks_tflops": {k: round(v, 3) for k, v in peaks.items()},
+        peak = derived[hp]
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get((hp, dom)),
+                "peak_source": (f"derived: {derived['sms']} SMs x {'128 FP32 lanes x 2 flops' if hp == 'fp32' else '2 FP64 FMA x 2 flops'}"
+                                f" x {derived['sm_max_ghz']:.3f} GHz"),
+                "cublas_gemm_tflops": {k: round(v, 3) for k, v in peaks.items()},
+                "frac_of_cublas_gemm": round(achieved / peaks[hp], 4) if peaks.get(hp) else None,
                 "per_launch_flops": per_launch_flops, "per_launch_ms": round(per_launch_ms, 4)}
     else:
         achieved = d["bytes"] / max(d["launches"], 1) / (per_launch_ms / 1e3) / 1e9
@@ -541,8 +561,70 @@ def precision_study(args):
     print(json.dumps(out))
 
 
+def truncation_study(args):
+    """The paper's truncation experiments (Sec. IV-V) on synthetic diamond cells,
+    every matrix from the library: S^-1 and S^-1 H errors and U unitarity vs
+    range, S^-1 H error vs system size, unitarity vs time step and Taylor terms,
+    and the spectrum vs the density-matrix range."""
+    import synth
+
+    import paper_1404_5776_gb300 as rtm
+    from paper_1404_5776_gb300 import spectra, studies
+    rtm.build()
+    t_start = time.perf_counter()
+    out = {"study": "truncation", "data": "synthetic (seeded diamond-lattice Gaussian model)", "r_S": 7.0,
+           "r_H": 7.0}
+    # range sweeps (r_Sinv = r_T = r_U = r); the last radius covers every pair (dense)
+    for ncell, basis, radii in ((3, "spd13", [3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 10.0, 12.0, 15.0]),
+                                (4, "sp4", [3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 10.0, 12.0, 19.0])):
+        s = synth.diamond_system(ncell, basis, 7.0, 7.0)
+        out[f"range_{basis}_{s.n_atoms}"] = studies.truncation_sweep(rtm, s, radii)
+    # size dependence at fixed ranges
+    systems = [synth.diamond_system(nc, "sp4", 7.0, 7.0) for nc in (2, 3, 4, 5)]
+    out["size_sp4_rSinv6_rT6"] = studies.size_sweep(rtm, systems, r_Sinv=6.0, r_T=6.0)
+    # time step and Taylor terms (64 atoms, every pair kept)
+    s = synth.diamond_system(2, "sp4", 7.0, 7.0)
+    out["unitarity_dt_terms"] = studies.unitarity_vs_dt_terms(
+        rtm, s, [0.01, 0.02, 0.05, 0.1, 0.15, 0.2], [2, 3, 4, 5, 6, 7, 8], r=12.0)
+    # density-matrix range: delta kick, U built once (H constant after the kick), 2000 steps
+    s = synth.diamond_system(3, "sp4", 7.0, 7.0)
+    K0, _, gap = synth.ground_state_dense(s, s.n // 2)
+    steps, kappa, dt = 2000, 1e-3, 0.05
+    omegas = np.linspace(0.0, 3.0, 601)[1:]
+    spec = {}
+    for rk in (4.0, 6.0, 8.0, 10.0, 15.0):
+        ctx = rtm.RT(s, dt=dt, full_step=0, obs_capacity=steps + 8, r_Sinv=10.0, r_T=10.0, r_U=10.0, r_K=rk,
+                     r_M=rk)
+        ctx.inverse()
+        ctx.set_density_dense(0, 0, K0)
+        q0 = float(np.sum(K0 * s.to_dense("S").T))
+        ctx.kick(0, 0, 0, kappa)
+        ctx.propagator(0.0)
+        ctx.step(steps)
+        obs = ctx.observables(0, 0)
+        blocks = ctx.pattern(0, rtm.RT_PAT_K)[1].size / s.n_atoms
+        ctx.close()
+        t = obs[:, 0]
+        alpha = spectra.polarizability(t, obs[:, 3] - obs[0, 3], kappa, omegas, damping=0.05)
+        Sw = spectra.strength_function(omegas, [alpha, 0 * alpha, 0 * alpha])
+        spec[rk] = (Sw, {"r_K": rk, "blocks_per_atom_K": blocks,
+                         "charge_step1_minus_exact_K0": float(obs[0, 1] - q0),
+                         "charge_drift": float(np.abs(obs[:, 1] - obs[0, 1]).max()),
+                         "f_sum": spectra.f_sum(omegas, Sw), "peaks": spectra.peaks(omegas, Sw, 4).tolist()})
+    ref = spec[15.0][0]
+    out["spectrum_vs_r_K"] = {
+        "system": f"{s.n_atoms} atoms sp4, gap {gap:.4f} Ha, kick {kappa} x, dt {dt}, {steps} steps, damping 0.05",
+        "runs": [dict(v[1], rel_l2_vs_dense=float(np.linalg.norm(v[0] - ref) / np.linalg.norm(ref)))
+                 for v in spec.values()]}
+    out["wall_s"] = round(time.perf_counter() - t_start, 1)
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.study == "truncation":
+        truncation_study(args)
+        return
     if args.precision_study:
         precision_study(args)
         return
