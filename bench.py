@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--foe-order", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
-    ap.add_argument("--study", default=None, choices=["truncation"],
+    ap.add_argument("--study", default=None, choices=["truncation", "scaling"],
                     help="run a study instead of the benchmark and print its JSON line")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NSTEPS",
                     help="instead of timing: run both paths NSTEPS steps and report their agreement")
@@ -620,10 +620,79 @@ def truncation_study(args):
     print(json.dumps(out))
 
 
+def scaling_study(args):
+    """Linear-scaling sweep (4-function diamond cells from 4096 to 32768 atoms,
+    r = 8 A, x kick): time per full step of the FP64 and mixed paths, device
+    memory and the mixed path's dipole agreement, against the atom count."""
+    import torch
+
+    import synth
+
+    import paper_1404_5776_gb300 as rtm
+    rtm.build()
+    basis = "sp4"
+    R = args.radius
+    small = argparse.Namespace(basis=basis)
+    mu, e_lo, e_hi = model_spectrum(small)
+    common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=64, r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
+    recs = []
+    t_start = time.perf_counter()
+    for ncell in (8, 10, 12, 14, 16):
+        t0 = time.perf_counter()
+        s = synth.diamond_system(ncell, basis, 7.0, 7.0)
+        t_build = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base_mem = torch.cuda.memory_allocated()
+        c64 = rtm.RT(s, precision="fp64", **common)
+        c64.inverse()
+        c64.ground_state(0, args.foe_order, mu, 0.01, e_lo, e_hi)
+        c64.kick(0, 0, 0, 1e-3)
+        K1 = c64.matrix(0, rtm.RT_MAT_K)
+        mem64 = (torch.cuda.max_memory_allocated() - base_mem) / 1e9
+        c32 = rtm.RT(s, precision="fp32", **common)
+        c32.inverse()
+        c32.set_density(0, 0, K1)
+        mem_both = (torch.cuda.max_memory_allocated() - base_mem) / 1e9
+        res = {}
+        for name, ctx in (("fp64", c64), ("mixed", c32)):
+            ctx.step(args.warmup)
+            ctx.synchronize()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.step(args.steps)
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / args.steps
+        o64, o32 = c64.observables(0, 0), c32.observables(0, 0)
+        p64, p32 = o64[:, 3], o32[:, 3]
+        ind = np.abs(p64 - p64[0]).max()
+        f64, _ = c64.step_work()
+        recs.append({"n_atoms": s.n_atoms, "n": int(s.n), "blocks_per_atom_K": c64.pattern(0, rtm.RT_PAT_K)[1].size / s.n_atoms,
+                     "ms_per_step_fp64": round(res["fp64"], 3), "ms_per_step_mixed": round(res["mixed"], 3),
+                     "us_per_atom_step_mixed": round(1e3 * res["mixed"] / s.n_atoms, 4),
+                     "gflops_fp64": round(f64 / res["fp64"] / 1e6, 1), "gflops_mixed": round(f64 / res["mixed"] / 1e6, 1),
+                     "device_gb_fp64_context": round(mem64, 3), "device_gb_both_contexts": round(mem_both, 3),
+                     "dipole_err_rel_P": float(np.abs(p32 - p64).max() / np.abs(p64).max()),
+                     "dipole_err_rel_induced": float(np.abs(p32 - p64).max() / ind) if ind > 0 else None,
+                     "compared_steps": int(min(len(p64), len(p32))), "host_build_s": round(t_build, 1)})
+        c64.close()
+        c32.close()
+        del K1
+        torch.cuda.empty_cache()
+    out = {"study": "scaling", "workload": f"diamond cells, {basis}, r_S=r_H=7A, all step radii {R:g}A, EM, x-kick 1e-3",
+           "steps": args.steps, "warmup": args.warmup, "runs": recs, "wall_s": round(time.perf_counter() - t_start, 1)}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.study == "truncation":
         truncation_study(args)
+        return
+    if args.study == "scaling":
+        scaling_study(args)
         return
     if args.precision_study:
         precision_study(args)
