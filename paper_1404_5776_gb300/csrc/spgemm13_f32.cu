@@ -6,17 +6,21 @@
 //   * FP32 matrices of 13-function atoms are stored with a padded row stride
 //     of 16 (one block = 13 x 16 elements = 832 B real / 1664 B complex, 16 B
 //     aligned), the same layout the blocks take in shared memory;
-//   * one warp owns one 13x13 output block; one elected lane streams the A and
-//     B blocks of the next NT triples into shared memory with 1D TMA bulk
-//     copies (cp.async.bulk) completing on a per-stage mbarrier (two stages:
-//     the next group is in flight while the current one is multiplied);
-//   * the warp splits into NT lane groups that take interleaved triples
-//     (complex: 2 groups of 16 lanes, real: 4 groups of 8 lanes); a lane keeps
-//     one (complex) or two (real) output columns and the matching B column(s)
-//     in registers and reads the A rows as shared-memory broadcasts;
+//   * one warp owns one 13x13 output block; one elected lane arms the stage's
+//     mbarrier and lanes 0..2NT-1 stream the A and B blocks of the next NT
+//     triples into shared memory with 1D TMA bulk copies (cp.async.bulk),
+//     two stages per warp (the next group is in flight while the current one
+//     is multiplied);
+//   * the warp splits into NT lane groups, one staged triple each (complex:
+//     2 groups of 16 lanes, 1 output column per lane; real: 4 groups of 8
+//     lanes, each lane 7 rows x 4 columns); a lane keeps its B columns in
+//     registers and reads the A rows as shared-memory broadcasts (one 16-byte
+//     skew per slot puts the groups' broadcasts on different banks);
+//   * the groups' partial sums meet in shared memory, and the epilogue walks
+//     the block's 169 elements with all 32 lanes (FP64 K blocks are read and
+//     written contiguously);
 //   * B^dagger operands are pre-transposed (a conjugate-transposed copy of
 //     U - I), so every staged block is a straight copy;
-//   * the groups' partial sums meet through warp shuffles at the end;
 //   * every wait on an mbarrier is bounded: on expiry the kernel records an
 //     error code, waits (bounded) for its copies in flight and returns.
 #include "rt_internal.cuh"
@@ -89,12 +93,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 // at k*STRIDE and B at k*STRIDE + SB).  Lane 0 arms the stage's mbarrier with
 // the byte count; then lanes 0..2NT-1 issue one bulk copy each (all copies in
 // one warp-wide instruction).  `blk` is the lane's block index for this group,
-// loaded one group ahead (-1: past the end, copy a zero block).
+// loaded one group ahead (-1: past the end of the item: copy a zero block, so
+// that every lane group multiplies without a branch).
 template <typename V, int NT>
 __device__ __forceinline__ void issue_group(V* buf, const V* __restrict__ A, const V* __restrict__ B, int blk,
                                             const V* __restrict__ zero, uint64_t* bar, int lane) {
   constexpr unsigned BYTES = SB * sizeof(V);
-  if (lane == 0) mbar_expect_tx(bar, NT * 2 * BYTES);
+  if (lane == 0) mbar_expect_tx(bar, NT * 2u * BYTES);
   __syncwarp();
   if (lane < 2 * NT) {
     const int k = lane >> 1;
@@ -118,8 +123,57 @@ struct Smem {
   uint64_t bar[WARPS][2];
 };
 
+// Elements of a 13 x 13 block handled by one lane in the per-element epilogues.
+constexpr int EPT = (NE + 31) / 32;
+
 // ---------------------------------------------------------------------------
-// complex: 2 groups x 16 lanes, lane (h, c) owns output column c (c < 13)
+// Main loop shared by both kernels: stream the item's triples through the
+// warp's two stages, NT triples per stage (lane group h takes slot h), and
+// call `mac(sA, sB)` on each staged pair.  Returns false if a wait expired
+// (copies in flight have then been drained, bounded).
+// ---------------------------------------------------------------------------
+template <typename V, int NT, typename F>
+__device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* __restrict__ A,
+                                               const V* __restrict__ B, const V* __restrict__ Z,
+                                               const int2* __restrict__ ab, int64_t t0, int64_t t1, int lane,
+                                               int h, F&& mac) {
+  constexpr int WBUF = NT * Slot<V>::STRIDE;
+  unsigned phase = 0u;    // bit s: parity to wait for on stage s
+  unsigned pending = 0u;  // bit s: copies in flight into stage s
+  int stage = 0;
+  int nblk = -1;  // this lane's block index for the next group (prefetched)
+  if (t0 < t1) {
+    issue_group<V, NT>(wsm, A, B, group_block<NT>(ab, t0, t1, lane), Z, &bar[0], lane);
+    nblk = group_block<NT>(ab, t0 + NT, t1, lane);
+    pending |= 1u;
+  }
+  for (int64_t tb = t0; tb < t1; tb += NT) {
+    if (tb + NT < t1) {
+      issue_group<V, NT>(wsm + (stage ^ 1) * WBUF, A, B, nblk, Z, &bar[stage ^ 1], lane);
+      nblk = group_block<NT>(ab, tb + 2 * NT, t1, lane);  // used one iteration later
+      pending |= 1u << (stage ^ 1);
+    }
+    if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
+      // bounded drain of every stage with copies in flight (this one included)
+      for (int st = 0; st < 2; ++st)
+        if ((pending >> st) & 1u) mbar_wait(&bar[st], (phase >> st) & 1u);
+      return false;
+    }
+    phase ^= 1u << stage;
+    pending &= ~(1u << stage);
+    const V* sA = wsm + stage * WBUF + h * Slot<V>::STRIDE;
+    mac(sA, sA + SB);
+    __syncwarp();  // all lanes done with this stage before it is refilled
+    stage ^= 1;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// complex: 2 lane groups x 16 lanes; lane (h, c) owns output column c of the
+// triple in slot h (columns 13..15 are padding: zero B columns, sums
+// dropped).  Partial sums meet in shared memory; the epilogue then walks the
+// 169 elements of the block with all 32 lanes.
 // ---------------------------------------------------------------------------
 template <int EPI>
 __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
@@ -142,84 +196,71 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
   }
   __syncwarp();
 
-  const float2* __restrict__ A = static_cast<const float2*>(g.A);
-  const float2* __restrict__ B = static_cast<const float2*>(g.B);
-  const float2* __restrict__ Z = static_cast<const float2*>(g.zero);
-  const int64_t t0 = g.ptr[item], t1 = g.ptr[item + 1];
-
   float2 acc[BS];
 #pragma unroll
   for (int r = 0; r < BS; ++r) acc[r] = make_float2(0.f, 0.f);
 
-  unsigned phase = 0u;    // bit s: parity to wait for on stage s
-  unsigned pending = 0u;  // bit s: copies in flight into stage s
-  bool ok = true;
-  int stage = 0;
-  int nblk = -1;  // this lane's block index for the next group (prefetched)
-  if (t0 < t1) {
-    issue_group<float2, NT>(wsm, A, B, group_block<NT>(g.ab, t0, t1, lane), Z, &bar[0], lane);
-    nblk = group_block<NT>(g.ab, t0 + NT, t1, lane);
-    pending |= 1u;
-  }
-  for (int64_t tb = t0; tb < t1; tb += NT) {
-    if (tb + NT < t1) {
-      issue_group<float2, NT>(wsm + (stage ^ 1) * WBUF, A, B, nblk, Z, &bar[stage ^ 1], lane);
-      nblk = group_block<NT>(g.ab, tb + 2 * NT, t1, lane);  // used one iteration later
-      pending |= 1u << (stage ^ 1);
-    }
-    if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
-      ok = false;
-      break;
-    }
-    phase ^= 1u << stage;
-    pending &= ~(1u << stage);
-    const float2* sA = wsm + stage * WBUF + h * Slot<float2>::STRIDE;
-    const float2* sB = sA + SB;
-    float2 bcol[BS];
-    // lanes c = 13..15 read the zero padding columns (their sums are dropped)
+  const bool ok = stream_triples<float2, NT>(
+      wsm, bar, static_cast<const float2*>(g.A), static_cast<const float2*>(g.B),
+      static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h,
+      [&](const float2* sA, const float2* sB) {
+        float2 bcol[BS];
 #pragma unroll
-    for (int m = 0; m < BS; ++m) bcol[m] = sB[m * RS + c];
+        for (int m = 0; m < BS; ++m) bcol[m] = sB[m * RS + c];
 #pragma unroll
-    for (int r = 0; r < BS; ++r) {
-      const float4* row = reinterpret_cast<const float4*>(sA + r * RS);
-      float2 v = acc[r];
+        for (int r = 0; r < BS; ++r) {
+          const float4* row = reinterpret_cast<const float4*>(sA + r * RS);
+          float2 v = acc[r];
 #pragma unroll
-      for (int m2 = 0; m2 < 7; ++m2) {
-        float4 a2 = row[m2];  // elements 2*m2, 2*m2+1 (broadcast)
-        v = cfma2(make_float2(a2.x, a2.y), bcol[2 * m2], v);
-        if (2 * m2 + 1 < BS) v = cfma2(make_float2(a2.z, a2.w), bcol[2 * m2 + 1], v);
-      }
-      acc[r] = v;
-    }
-    __syncwarp();  // all lanes done with this stage before it is refilled
-    stage ^= 1;
-  }
+          for (int m2 = 0; m2 < 7; ++m2) {
+            const float4 a2 = row[m2];  // A[r][2m2], A[r][2m2+1] (broadcast in the group)
+            v = cfma2(make_float2(a2.x, a2.y), bcol[2 * m2], v);
+            if (2 * m2 + 1 < BS) v = cfma2(make_float2(a2.z, a2.w), bcol[2 * m2 + 1], v);
+          }
+          acc[r] = v;
+        }
+      });
   if (!ok) {
-    // bounded drain of copies in flight, then report and leave
-    for (int s = 0; s < 2; ++s)
-      if ((pending >> s) & 1u) mbar_wait(&bar[s], (phase >> s) & 1u);
     if (lane == 0 && g.err) atomicExch(g.err, 1);
     return;
   }
-  // the two groups meet
+  // partial sums of the two groups to shared memory (every copy has landed)
+  float2* part = wsm;  // [NT][BS][RS]
 #pragma unroll
-  for (int r = 0; r < BS; ++r) {
-    acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, 16);
-    acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, 16);
+  for (int r = 0; r < BS; ++r) part[h * SB + r * RS + c] = acc[r];
+  __syncwarp();
+  float2 sum[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int e = lane + 32 * k;
+    sum[k] = make_float2(0.f, 0.f);
+    if (e < NE) {
+      const int r = e / BS, c = e - BS * r;
+#pragma unroll
+      for (int hh = 0; hh < NT; ++hh) {
+        const float2 v = part[hh * SB + r * RS + c];
+        sum[k].x += v.x;
+        sum[k].y += v.y;
+      }
+    }
   }
   const int q = g.item_blk[item];
   if constexpr (EPI == EPI_STORE || EPI == EPI_ADD) {
     float2* __restrict__ C = static_cast<float2*>(g.C);
-    if (h == 0 && c < BS) {
-      if constexpr (EPI == EPI_ADD) {  // C += acc (all loads first)
-        float2 old[BS];
+    if constexpr (EPI == EPI_ADD) {  // C += acc (all loads first)
+      float2 old[EPT];
 #pragma unroll
-        for (int r = 0; r < BS; ++r) old[r] = C[(int64_t)q * SB + r * RS + c];
-#pragma unroll
-        for (int r = 0; r < BS; ++r) acc[r] = make_float2(old[r].x + acc[r].x, old[r].y + acc[r].y);
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        old[k] = e < NE ? C[(int64_t)q * SB + (e / BS) * RS + e % BS] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int r = 0; r < BS; ++r) C[(int64_t)q * SB + r * RS + c] = acc[r];
+      for (int k = 0; k < EPT; ++k) sum[k] = make_float2(sum[k].x + old[k].x, sum[k].y + old[k].y);
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = lane + 32 * k;
+      if (e < NE) C[(int64_t)q * SB + (e / BS) * RS + e % BS] = sum[k];
     }
     // delta form: also W = K + M in FP32 (K in FP64, dense blocks, through
     // the map from this pattern to K's; -1 = no K block).  In the incremental
@@ -230,19 +271,25 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
       const float2* __restrict__ Mh = static_cast<const float2*>(g.addend);
       float2* __restrict__ W = static_cast<float2*>(g.U);
       const int kq = g.add_map ? g.add_map[q] : q;
-      if (h == 0 && c < BS) {
-        double2 kv[BS];
-        float2 mh[BS];
+      double2 kv[EPT];
+      float2 mh[EPT];
 #pragma unroll
-        for (int r = 0; r < BS; ++r) {
-          kv[r] = (kq >= 0) ? Kb[(int64_t)kq * NE + r * BS + c] : make_double2(0.0, 0.0);
-          mh[r] = Mh ? Mh[(int64_t)q * SB + r * RS + c] : make_float2(0.f, 0.f);
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        kv[k] = make_double2(0.0, 0.0);
+        mh[k] = make_float2(0.f, 0.f);
+        if (e < NE) {
+          if (kq >= 0) kv[k] = Kb[(int64_t)kq * NE + e];
+          if (Mh) mh[k] = Mh[(int64_t)q * SB + (e / BS) * RS + e % BS];
         }
+      }
 #pragma unroll
-        for (int r = 0; r < BS; ++r)
-          W[(int64_t)q * SB + r * RS + c] =
-              make_float2((float)(((double)mh[r].x + (double)acc[r].x) + kv[r].x),
-                          (float)(((double)mh[r].y + (double)acc[r].y) + kv[r].y));
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < NE)
+          W[(int64_t)q * SB + (e / BS) * RS + e % BS] =
+              make_float2((float)(((double)mh[k].x + (double)sum[k].x) + kv[k].x),
+                          (float)(((double)mh[k].y + (double)sum[k].y) + kv[k].y));
       }
     }
   } else if constexpr (EPI == EPI_DELTA_SANDWICH) {
@@ -253,63 +300,73 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
     const double2* __restrict__ base = static_cast<const double2*>(g.base);
     const float2* __restrict__ add = static_cast<const float2*>(g.addend);
     const int aq = g.add_map ? g.add_map[q] : q;
-    double2 val[BS];
-    if (h == 0 && c < BS) {
-      // all loads first (K and its mirror may alias later stores)
-      float2 mv[BS];
+    double2 val[EPT];
+    float2 mv[EPT];
+    // all loads first (the stores of K below may alias them)
 #pragma unroll
-      for (int r = 0; r < BS; ++r) {
-        val[r] = base[(int64_t)q * NE + r * BS + c];
-        mv[r] = (aq >= 0) ? add[(int64_t)aq * SB + r * RS + c] : make_float2(0.f, 0.f);
+    for (int k = 0; k < EPT; ++k) {
+      const int e = lane + 32 * k;
+      val[k] = make_double2(0.0, 0.0);
+      mv[k] = make_float2(0.f, 0.f);
+      if (e < NE) {
+        val[k] = base[(int64_t)q * NE + e];
+        if (aq >= 0) mv[k] = add[(int64_t)aq * SB + (e / BS) * RS + e % BS];
       }
-      if (g.base2) {
-        // incremental form: dK' = dK + R + M_hi + M_lo + N_lo + N_hi, every
-        // part added in FP64 (the lo parts are below FP32 resolution of the hi)
-        const double2* __restrict__ R = static_cast<const double2*>(g.base2);
-        const float2* __restrict__ Nl = static_cast<const float2*>(g.addend2);
-        const float2* __restrict__ Ml = static_cast<const float2*>(g.addend3);
+    }
+    if (g.base2) {
+      // incremental form: dK' = dK + R + M_hi + M_lo + N_lo + N_hi, every
+      // part added in FP64 (the lo parts are below FP32 resolution of the hi)
+      const double2* __restrict__ R = static_cast<const double2*>(g.base2);
+      const float2* __restrict__ Nl = static_cast<const float2*>(g.addend2);
+      const float2* __restrict__ Ml = static_cast<const float2*>(g.addend3);
 #pragma unroll
-        for (int r = 0; r < BS; ++r) {
-          double2 rv = R[(int64_t)q * NE + r * BS + c];
-          float2 nl = Nl[(int64_t)q * SB + r * RS + c];
-          float2 ml = (aq >= 0) ? Ml[(int64_t)aq * SB + r * RS + c] : make_float2(0.f, 0.f);
-          val[r] = make_double2(val[r].x + rv.x + (((double)nl.x + (double)ml.x) + (double)acc[r].x),
-                                val[r].y + rv.y + (((double)nl.y + (double)ml.y) + (double)acc[r].y));
-          acc[r] = make_float2(0.f, 0.f);
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < NE) {
+          const int o = (e / BS) * RS + e % BS;
+          const double2 rv = R[(int64_t)q * NE + e];
+          const float2 nl = Nl[(int64_t)q * SB + o];
+          const float2 ml = (aq >= 0) ? Ml[(int64_t)aq * SB + o] : make_float2(0.f, 0.f);
+          val[k] = make_double2(val[k].x + rv.x + (((double)nl.x + (double)ml.x) + (double)sum[k].x),
+                                val[k].y + rv.y + (((double)nl.y + (double)ml.y) + (double)sum[k].y));
+          sum[k] = make_float2(0.f, 0.f);
         }
       }
-#pragma unroll
-      for (int r = 0; r < BS; ++r)
-        val[r] = make_double2(val[r].x + ((double)mv[r].x + (double)acc[r].x),
-                              val[r].y + ((double)mv[r].y + (double)acc[r].y));
     }
-    if (i != j) {
-      if (h == 0 && c < BS) {
-        const int qt = g.tmap[q];
 #pragma unroll
-        for (int r = 0; r < BS; ++r) {
-          K[(int64_t)q * NE + r * BS + c] = val[r];
-          K[(int64_t)qt * NE + c * BS + r] = make_double2(val[r].x, -val[r].y);
+    for (int k = 0; k < EPT; ++k)
+      val[k] = make_double2(val[k].x + ((double)mv[k].x + (double)sum[k].x),
+                            val[k].y + ((double)mv[k].y + (double)sum[k].y));
+    if (i != j) {
+      const int qt = g.tmap[q];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < NE) {
+          const int r = e / BS, c = e - BS * r;
+          K[(int64_t)q * NE + e] = val[k];
+          K[(int64_t)qt * NE + c * BS + r] = make_double2(val[k].x, -val[k].y);
         }
       }
     } else {
-      // pair (r,c) with (c,r) through shared memory (this warp's staging area;
-      // every copy into it has completed)
-      double2* sK = reinterpret_cast<double2*>(wsm);
-      __syncwarp();
-      if (h == 0 && c < BS) {
+      // pair (r,c) with (c,r) through shared memory (after the partial sums)
+      double2* sK = reinterpret_cast<double2*>(part + NT * SB);
 #pragma unroll
-        for (int r = 0; r < BS; ++r) sK[r * BS + c] = val[r];
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < NE) sK[e] = val[k];
       }
       __syncwarp();
       double herm = 0.0;
-      if (h == 0 && c < BS) {
 #pragma unroll
-        for (int r = 0; r < BS; ++r) {
-          double2 tv = sK[c * BS + r];
-          double dr = val[r].x - tv.x, di = val[r].y + tv.y;
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < NE) {
+          const int r = e / BS, c = e - BS * r;
+          const double2 tv = sK[c * BS + r];
+          const double dr = val[k].x - tv.x, di = val[k].y + tv.y;
           herm = fmax(herm, sqrt(dr * dr + di * di));
-          K[(int64_t)q * NE + r * BS + c] = make_double2(0.5 * (val[r].x + tv.x), 0.5 * (val[r].y - tv.y));
+          K[(int64_t)q * NE + e] = make_double2(0.5 * (val[k].x + tv.x), 0.5 * (val[k].y - tv.y));
         }
       }
       for (int off = 16; off > 0; off >>= 1) herm = fmax(herm, __shfl_xor_sync(0xffffffffu, herm, off));
@@ -319,17 +376,23 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
 }
 
 // ---------------------------------------------------------------------------
-// real: 4 groups x 8 lanes, lane (h, cl) owns output columns 2cl and 2cl+1
+// real: 4 lane groups x 2 row halves x 4 lanes; lane (h, half, cl) owns
+// output rows 7 half .. 7 half + 6 and columns 4cl..4cl+3 of the triple in
+// slot h (the second half's seventh row would be row 13: it multiplies the
+// first row of the staged B block and is dropped).  Same staging and
+// epilogue scheme as above.
 // ---------------------------------------------------------------------------
 template <int EPI>
 __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_r32(GemmArgs g) {
   constexpr int NT = 4;
+  constexpr int RH = 7;  // rows per half
   constexpr int WBUF = NT * Slot<float>::STRIDE;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int h = lane >> 3;
-  const int cl = lane & 7;
-  const int c0 = 2 * cl, c1 = 2 * cl + 1;
+  const int half = (lane >> 2) & 1;
+  const int cl = lane & 3;
+  const int r0 = RH * half;
   const int64_t item = (int64_t)blockIdx.x * WARPS + warp;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   Smem* ctl = reinterpret_cast<Smem*>(dyn_smem);
@@ -343,134 +406,98 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_r32(GemmArgs g) {
   }
   __syncwarp();
 
-  const float* __restrict__ A = static_cast<const float*>(g.A);
-  const float* __restrict__ B = static_cast<const float*>(g.B);
-  const float* __restrict__ Z = static_cast<const float*>(g.zero);
-  const int64_t t0 = g.ptr[item], t1 = g.ptr[item + 1];
+  float4 acc[RH];
+#pragma unroll
+  for (int rr = 0; rr < RH; ++rr) acc[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  float acc0[BS], acc1[BS];
+  const bool ok = stream_triples<float, NT>(
+      wsm, bar, static_cast<const float*>(g.A), static_cast<const float*>(g.B), static_cast<const float*>(g.zero),
+      g.ab, g.ptr[item], g.ptr[item + 1], lane, h, [&](const float* sA, const float* sB) {
+        float4 b[BS];  // B[m][4cl .. 4cl+3]
 #pragma unroll
-  for (int r = 0; r < BS; ++r) acc0[r] = acc1[r] = 0.f;
-
-  unsigned phase = 0u;    // bit s: parity to wait for on stage s
-  unsigned pending = 0u;  // bit s: copies in flight into stage s
-  bool ok = true;
-  int stage = 0;
-  int nblk = -1;  // this lane's block index for the next group (prefetched)
-  if (t0 < t1) {
-    issue_group<float, NT>(wsm, A, B, group_block<NT>(g.ab, t0, t1, lane), Z, &bar[0], lane);
-    nblk = group_block<NT>(g.ab, t0 + NT, t1, lane);
-    pending |= 1u;
-  }
-  for (int64_t tb = t0; tb < t1; tb += NT) {
-    if (tb + NT < t1) {
-      issue_group<float, NT>(wsm + (stage ^ 1) * WBUF, A, B, nblk, Z, &bar[stage ^ 1], lane);
-      nblk = group_block<NT>(g.ab, tb + 2 * NT, t1, lane);  // used one iteration later
-      pending |= 1u << (stage ^ 1);
-    }
-    if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
-      ok = false;
-      break;
-    }
-    phase ^= 1u << stage;
-    pending &= ~(1u << stage);
-    const float* sA = wsm + stage * WBUF + h * Slot<float>::STRIDE;
-    const float* sB = sA + SB;
-    float b0[BS], b1[BS];
-    // columns c0, c1 <= 15: the padding columns 13..15 hold zeros (sums dropped)
+        for (int m = 0; m < BS; ++m) b[m] = *reinterpret_cast<const float4*>(sB + m * RS + 4 * cl);
 #pragma unroll
-    for (int m = 0; m < BS; ++m) {
-      float2 bb = *reinterpret_cast<const float2*>(sB + m * RS + c0);
-      b0[m] = bb.x;
-      b1[m] = bb.y;
-    }
+        for (int rr = 0; rr < RH; ++rr) {
+          const float4* row = reinterpret_cast<const float4*>(sA + (r0 + rr) * RS);
+          float4 v = acc[rr];
 #pragma unroll
-    for (int r = 0; r < BS; ++r) {
-      const float4* row = reinterpret_cast<const float4*>(sA + r * RS);
-      float v0 = acc0[r], v1 = acc1[r];
+          for (int m4 = 0; m4 < 4; ++m4) {
+            const float4 a4 = row[m4];  // A[r][4m4 .. 4m4+3] (broadcast in the half group)
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
-      for (int m4 = 0; m4 < 4; ++m4) {
-        float4 a4 = row[m4];
-        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          int m = 4 * m4 + u;
-          if (m < BS) {
-            v0 = fmaf(av[u], b0[m], v0);
-            v1 = fmaf(av[u], b1[m], v1);
+            for (int u = 0; u < 4; ++u) {
+              const int m = 4 * m4 + u;
+              if (m < BS) {
+                v.x = fmaf(av[u], b[m].x, v.x);
+                v.y = fmaf(av[u], b[m].y, v.y);
+                v.z = fmaf(av[u], b[m].z, v.z);
+                v.w = fmaf(av[u], b[m].w, v.w);
+              }
+            }
           }
+          acc[rr] = v;
         }
-      }
-      acc0[r] = v0;
-      acc1[r] = v1;
-    }
-    __syncwarp();
-    stage ^= 1;
-  }
+      });
   if (!ok) {
-    for (int s = 0; s < 2; ++s)
-      if ((pending >> s) & 1u) mbar_wait(&bar[s], (phase >> s) & 1u);
     if (lane == 0 && g.err) atomicExch(g.err, 1);
     return;
   }
+  float* part = wsm;  // [NT][BS][RS]
 #pragma unroll
-  for (int r = 0; r < BS; ++r) {
-    acc0[r] += __shfl_xor_sync(0xffffffffu, acc0[r], 8);
-    acc0[r] += __shfl_xor_sync(0xffffffffu, acc0[r], 16);
-    acc1[r] += __shfl_xor_sync(0xffffffffu, acc1[r], 8);
-    acc1[r] += __shfl_xor_sync(0xffffffffu, acc1[r], 16);
+  for (int rr = 0; rr < RH; ++rr)
+    if (r0 + rr < BS) *reinterpret_cast<float4*>(part + h * SB + (r0 + rr) * RS + 4 * cl) = acc[rr];
+  __syncwarp();
+  float sum[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int e = lane + 32 * k;
+    sum[k] = 0.f;
+    if (e < NE) {
+      const int r = e / BS, c = e - BS * r;
+#pragma unroll
+      for (int hh = 0; hh < NT; ++hh) sum[k] += part[hh * SB + r * RS + c];
+    }
   }
-  if (h != 0 || c0 >= BS) return;
   const int q = g.item_blk[item];
   float* __restrict__ C = static_cast<float*>(g.C);
   if constexpr (EPI == EPI_STORE) {
 #pragma unroll
-    for (int r = 0; r < BS; ++r) {
-      if (c1 < BS) *reinterpret_cast<float2*>(&C[(int64_t)q * SB + r * RS + c0]) = make_float2(acc0[r], acc1[r]);
-      else C[(int64_t)q * SB + r * RS + c0] = acc0[r];
+    for (int k = 0; k < EPT; ++k) {
+      const int e = lane + 32 * k;
+      if (e < NE) C[(int64_t)q * SB + (e / BS) * RS + e % BS] = sum[k];
     }
   } else if constexpr (EPI == EPI_STORE_ACC) {
-    // U += coef * C (coef real or imaginary); every load is issued before the
-    // first store so the read-modify-writes do not serialise on L2 round trips.
-    // C is not stored when g.C is null (the last power is needed only in U).
+    // U += coef * C (coef real or imaginary), every load before the first
+    // store; C is not stored when g.C is null (the last power is needed only
+    // in U), and the last power also writes U^dagger per block (g.base).
     float2* __restrict__ U = static_cast<float2*>(g.U);
     const int uq = g.umap ? g.umap[q] : q;
     const float cf = (float)g.coef;
     if (uq >= 0) {
-      float4 uv[BS];  // (U[r][c0], U[r][c1]) as 4 floats; c1 <= 13 stays inside the padded row
+      float2 uv[EPT];
 #pragma unroll
-      for (int r = 0; r < BS; ++r) uv[r] = *reinterpret_cast<const float4*>(&U[(int64_t)uq * SB + r * RS + c0]);
-#pragma unroll
-      for (int r = 0; r < BS; ++r) {
-        if (g.coef_imag) {
-          uv[r].y += cf * acc0[r];
-          uv[r].w += cf * acc1[r];
-        } else {
-          uv[r].x += cf * acc0[r];
-          uv[r].z += cf * acc1[r];
-        }
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        uv[k] = e < NE ? U[(int64_t)uq * SB + (e / BS) * RS + e % BS] : make_float2(0.f, 0.f);
       }
+      float2* __restrict__ UH = g.base ? static_cast<float2*>(const_cast<void*>(g.base)) : nullptr;
 #pragma unroll
-      for (int r = 0; r < BS; ++r) {
-        float2* dst = &U[(int64_t)uq * SB + r * RS + c0];
-        if (c1 < BS) *reinterpret_cast<float4*>(dst) = uv[r];
-        else *dst = make_float2(uv[r].x, uv[r].y);
-      }
-      // last power: U is complete; also write its conjugate transpose per block
-      if (g.base) {
-        float2* __restrict__ UH = static_cast<float2*>(const_cast<void*>(g.base));
-#pragma unroll
-        for (int r = 0; r < BS; ++r) {
-          UH[(int64_t)uq * SB + c0 * RS + r] = make_float2(uv[r].x, -uv[r].y);
-          if (c1 < BS) UH[(int64_t)uq * SB + c1 * RS + r] = make_float2(uv[r].z, -uv[r].w);
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < NE) {
+          const int r = e / BS, c = e - BS * r;
+          if (g.coef_imag) uv[k].y += cf * sum[k];
+          else uv[k].x += cf * sum[k];
+          U[(int64_t)uq * SB + r * RS + c] = uv[k];
+          if (UH) UH[(int64_t)uq * SB + c * RS + r] = make_float2(uv[k].x, -uv[k].y);
         }
       }
     }
     if (C) {
 #pragma unroll
-      for (int r = 0; r < BS; ++r) {
-        if (c1 < BS) *reinterpret_cast<float2*>(&C[(int64_t)q * SB + r * RS + c0]) = make_float2(acc0[r], acc1[r]);
-        else C[(int64_t)q * SB + r * RS + c0] = acc0[r];
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < NE) C[(int64_t)q * SB + (e / BS) * RS + e % BS] = sum[k];
       }
     }
   }
