@@ -146,6 +146,18 @@ typedef struct {
                                first step after K or U changed, with
                                R = U K_ref U^dagger - K_ref in FP64 and U - I as
                                FP32 hi + lo; 13-function systems only          */
+  int32_t field_poly;       /* EM only: build U(t) each step as the polynomial
+                               U = sum_m E^m V_m in the field value E = E(t+dt/2).
+                               H = H0 - E D and every cut being linear, the
+                               truncated powers are T^n(E) = sum_m E^m Q_{n,m}
+                               with Q_{1,0} = cut(S^-1 H0), Q_{1,1} = -cut(S^-1 D),
+                               Q_{n,m} = cut(Q_{1,0} Q_{n-1,m}) + cut(Q_{1,1} Q_{n-1,m-1});
+                               V_m = sum_n c_n Q_{n,m} (+ I in V_0) are formed in
+                               FP64 once by rt_inverse (and again when the field
+                               axis changes).  The same U as the literal series up
+                               to rounding, in FP64 in either precision; holds
+                               (taylor_terms + 1) complex FP64 matrices on P_U and
+                               twice that many real ones while they are formed  */
 } rt_params;
 
 typedef struct {
@@ -156,7 +168,7 @@ typedef struct {
 
 /* Fills the defaults: radii 8 A, dt 0.05, EM, 6 Taylor terms, tol 1e-10,
  * maxit 100, 2 CN iterations per step, FP64, full step, 1 kick, 12 kick terms,
- * 4096 observable steps, graphs on, incremental form off. */
+ * 4096 observable steps, graphs on, incremental form and field polynomial off. */
 RT_API rt_status rt_default_params(rt_params* p);
 
 /* Creates a context for n_sys systems: validates and copies the host inputs,

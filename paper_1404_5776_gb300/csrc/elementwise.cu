@@ -735,4 +735,67 @@ void launch_zaxpy(double2* z, const double2* x, const double2* y, double a, int6
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// field polynomial of the EM propagator
+// ---------------------------------------------------------------------------
+__global__ void k_acc_real(double2* __restrict__ V, const double* __restrict__ Q, const int32_t* __restrict__ map,
+                           int64_t nnzb_v, int NE, double coef, int imag) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; idx < nnzb_v * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx / NE;
+    int e = (int)(idx - q * NE);
+    int sq = map ? map[q] : (int)q;
+    if (sq < 0) continue;
+    double v = coef * Q[(int64_t)sq * NE + e];
+    if (imag) V[idx].y += v;
+    else V[idx].x += v;
+  }
+}
+
+void launch_acc_real(double2* V, const double* Q, const int32_t* map, int64_t nnzb_v, int B, double coef, int imag,
+                     cudaStream_t st) {
+  int64_t n = nnzb_v * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_acc_real<<<(unsigned)g, 256, 0, st>>>(V, Q, map, nnzb_v, B * B, coef, imag);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+__global__ void k_field_poly(PolyTerms V, int deg, const DevState* __restrict__ s, int which, double2* __restrict__ U,
+                             float2* __restrict__ dU, float2* __restrict__ dUH, int64_t nnzb,
+                             const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B, int rs) {
+  const double E = s->E[which];
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    double2 u = V.v[deg][idx];
+    for (int m = deg - 1; m >= 0; --m) {
+      const double2 vm = V.v[m][idx];
+      u = make_double2(u.x * E + vm.x, u.y * E + vm.y);
+    }
+    if (U) U[idx] = u;
+    if (dU) {
+      const int64_t q = idx / NE;
+      const int e = (int)(idx - q * NE);
+      const int r = e / B, c = e - r * B;
+      const double d = (rowidx[q] == col[q] && r == c) ? 1.0 : 0.0;
+      const float2 f = make_float2((float)(u.x - d), (float)u.y);
+      dU[q * (int64_t)B * rs + r * rs + c] = f;
+      if (dUH) dUH[q * (int64_t)B * rs + c * rs + r] = make_float2(f.x, -f.y);
+    }
+  }
+}
+
+void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which, double2* U, float2* dU,
+                       float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st) {
+  RT_REQUIRE(deg >= 0 && deg < RT_MAX_POLY, RT_EINTERNAL, "field polynomial degree out of range");
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_field_poly<<<(unsigned)g, 256, 0, st>>>(V, deg, s, which, U, dU, dUH, nnzb, rowidx, col, B, rs32(B));
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
 }  // namespace rt

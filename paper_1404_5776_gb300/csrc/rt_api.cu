@@ -27,10 +27,11 @@ namespace rt {
 int64_t triple_true_macs(const Triples& T, const Pattern& A, bool a_dag, const Pattern& C, const int32_t* bsize,
                          Arena& arena, cudaStream_t st);
 
-enum ProfClass { PC_FIELD = 0, PC_T, PC_TAYLOR, PC_UK, PC_MUDAG, PC_CN_HOT, PC_CN_U, PC_OBS, PC_MISC, PC_N };
+enum ProfClass { PC_FIELD = 0, PC_T, PC_TAYLOR, PC_UK, PC_MUDAG, PC_CN_HOT, PC_CN_U, PC_OBS, PC_MISC, PC_POLY, PC_N };
 static const char* kProfNames[PC_N] = {"field_update", "gemm_T=SinvH",  "gemm_taylor_powers",
                                        "gemm_M=UK",    "gemm_K=MUdag",  "gemm_cn_hotelling",
-                                       "gemm_cn_U=XB", "traces",        "misc"};
+                                       "gemm_cn_U=XB", "traces",        "misc",
+                                       "field_polynomial_U"};
 
 struct TripleKey {
   const Pattern *A, *B, *C;
@@ -67,6 +68,10 @@ struct Sys {
   double *S = nullptr, *H0 = nullptr, *D[3] = {nullptr, nullptr, nullptr}, *Hm = nullptr;
   double *Sinv = nullptr, *Zs = nullptr, *Xs2 = nullptr;
   double *T = nullptr, *P0 = nullptr, *P1 = nullptr, *T0 = nullptr, *TD = nullptr, *T2 = nullptr;
+  // field polynomial of the EM propagator: U(E) = sum_m E^m V[m]
+  std::vector<double2*> V;
+  std::vector<double*> Qa, Qb;  // coefficient matrices of two consecutive powers while V is formed
+  double* TDn = nullptr;        // -cut(S^-1 D)
   double2 *U = nullptr, *M = nullptr;
   std::vector<double2*> K;
   double2 *Acn = nullptr, *Bcn = nullptr, *X = nullptr, *Xn = nullptr, *Zc = nullptr;
@@ -468,6 +473,12 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
       s.TD = c->arena.get_n<double>(nvals(s, s.pT));
     }
   }
+  if (p.field_poly) {
+    RT_REQUIRE(p.prop == RT_PROP_EM, RT_EINVAL, "the field polynomial is defined for the EM propagator");
+    if (!s.T0) s.T0 = c->arena.get_n<double>(nvals(s, s.pT));
+    s.TDn = c->arena.get_n<double>(nvals(s, s.pT));
+    for (int m = 0; m < p.taylor_terms; ++m) s.V.push_back(c->arena.get_n<double2>(nvals(s, s.pU)));
+  }
   if (p.incremental) {
     // incremental form for a constant propagator (13-function blocks)
     RT_REQUIRE(s.B == 13, RT_EINVAL, "the incremental form needs 13-function atoms (block size 13)");
@@ -495,6 +506,8 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
   }
   RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
 }
+
+static void build_field_poly(rt_ctx* c, Sys& s);
 
 // ----------------------------------------------------------------------------
 // Hotelling inverse of S (Sec. V.A), cut to r_Sinv
@@ -555,6 +568,7 @@ static rt_status hotelling_sinv(rt_ctx* c, Sys& s) {
     gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.H0, s.T0), s.pT);
     gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.D[c->field.dir], s.TD), s.pT);
   }
+  if (c->p.field_poly) build_field_poly(c, s);
   RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
   c->graph_dirty = true;
   return status;
@@ -695,8 +709,74 @@ static void build_m4(rt_ctx* c, Sys& s) {
   }
 }
 
+// Coefficients of the EM propagator as a polynomial in the field value E
+// (H = H0 - E D, eq. EM with every product cut as in the literal series):
+// T(E) = Q_{1,0} + E Q_{1,1} with Q_{1,0} = cut(S^-1 H0), Q_{1,1} = -cut(S^-1 D);
+// T^n(E) = cut(T(E) T^{n-1}(E)) = sum_m E^m Q_{n,m} with
+// Q_{n,m} = cut(Q_{1,0} Q_{n-1,m}) + cut(Q_{1,1} Q_{n-1,m-1}) (the cut is linear);
+// U(E) = I + sum_n c_n T^n(E) = sum_m E^m V_m, V_m = sum_n c_n Q_{n,m} (+ I in V_0).
+static void build_field_poly(rt_ctx* c, Sys& s) {
+  const rt_params& p = c->p;
+  const int deg = p.taylor_terms - 1;
+  Pattern* PT = s.pT;
+  Pattern* PU = s.pU;
+  const size_t nT = nvals(s, PT), nU = nvals(s, PU);
+  TripleInfo& tT = triples_for(c, s, s.pSinv, false, s.pH, false, PT, false);
+  gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.H0, s.T0), PT);
+  gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.D[c->field.dir], s.TDn), PT);
+  launch_scale(s.TDn, -1.0, (int64_t)nT, c->ws);
+  launch_identity(reinterpret_cast<double*>(s.V[0]), true, PU->nnzb, PU->rowidx, PU->col, s.B, 1.0, c->ws);
+  for (int m = 1; m <= deg; ++m) RT_CUDA_CHECK(cudaMemsetAsync(s.V[m], 0, sizeof(double2) * nU, c->ws));
+  if (deg >= 1) {
+    double c1 = 0.0;
+    int i1 = 0;
+    taylor_coef(1, p.dt, &c1, &i1);
+    launch_acc_real(s.V[0], s.T0, s.u_to_t, PU->nnzb, s.B, c1, i1, c->ws);
+    launch_acc_real(s.V[1], s.TDn, s.u_to_t, PU->nnzb, s.B, c1, i1, c->ws);
+  }
+  if (deg >= 2 && s.Qa.empty())
+    for (int m = 0; m <= deg; ++m) {
+      s.Qa.push_back(c->arena.get_n<double>(nU));
+      s.Qb.push_back(c->arena.get_n<double>(nU));
+    }
+  TripleInfo& t2 = triples_for(c, s, PT, false, PT, false, PU, false);
+  TripleInfo& tn = triples_for(c, s, PT, false, PU, false, PU, false);
+  std::vector<const double*> prev = {s.T0, s.TDn};
+  for (int n = 2; n <= deg; ++n) {
+    TripleInfo& tl = n == 2 ? t2 : tn;
+    double cn = 0.0;
+    int ci = 0;
+    taylor_coef(n, p.dt, &cn, &ci);
+    std::vector<double*>& out = (n % 2 == 0) ? s.Qa : s.Qb;
+    for (int m = 0; m <= n; ++m) {
+      bool first = true;
+      if (m <= n - 1) {
+        gemm(c, s, PC_MISC, tl, false, false, false, false, EPI_STORE, args(s.T0, prev[m], out[m]), PU);
+        first = false;
+      }
+      if (m >= 1)
+        gemm(c, s, PC_MISC, tl, false, false, false, false, first ? EPI_STORE : EPI_ADD,
+             args(s.TDn, prev[m - 1], out[m]), PU);
+      launch_acc_real(s.V[m], out[m], nullptr, PU->nnzb, s.B, cn, ci, c->ws);
+    }
+    prev.assign(out.begin(), out.begin() + n + 1);
+  }
+}
+
 static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
   const rt_params& p = c->p;
+  if (p.prop == RT_PROP_EM && p.field_poly) {
+    PolyTerms V;
+    memset(&V, 0, sizeof(V));
+    const int deg = p.taylor_terms - 1;
+    for (int m = 0; m <= deg; ++m) V.v[m] = s.V[m];
+    const double nU = (double)nvals(s, s.pU);
+    run(c, PC_POLY, 0, 16.0 * nU * (deg + 2), [&] {  // read V_0..V_deg, write U (or dU and dU^dagger)
+      launch_field_poly(V, deg, c->dstate, E_MID, fp32 ? nullptr : s.U, fp32 ? s.dUf : nullptr,
+                        fp32 ? s.dUH : nullptr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
+    });
+    return;
+  }
   if (p.prop == RT_PROP_EM) {
     if (fp32) {
       // T(t+dt/2) = T0 - E T_D (linearity of the cut product in E)
@@ -1195,6 +1275,9 @@ rt_status rt_set_field(rt_ctx* c, const rt_field* f) {
         gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.D[c->field.dir], s.TD), s.pT);
       }
     }
+    if (dir_changed && c->p.field_poly)
+      for (auto& sp : c->sys)
+        if (sp->sinv_ready) build_field_poly(c, *sp);
     return RT_OK;
   });
 }

@@ -52,6 +52,18 @@ void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const 
 void launch_split_u_hilo(const double2* U, float2* hi, float2* lo, int64_t nnzb, const int32_t* rowidx,
                          const int32_t* col, int B, cudaStream_t st);
 void launch_zaxpy(double2* z, const double2* x, const double2* y, double a, int64_t n, cudaStream_t st);
+// V[q] += coef * Q[map[q]] (real Q into the real or, with imag, the imaginary part of V; map null = same
+// blocks, -1 = no block)
+void launch_acc_real(double2* V, const double* Q, const int32_t* map, int64_t nnzb_v, int B, double coef, int imag,
+                     cudaStream_t st);
+constexpr int RT_MAX_POLY = 32;
+struct PolyTerms {
+  const double2* v[RT_MAX_POLY];
+};
+// U = sum_{m<=deg} E^m V_m at E = s->E[which] (Horner, FP64); writes U (FP64, if non-null) and/or
+// dU = U - I with its per-block conjugate transpose dUH in FP32 (padded rows), if non-null
+void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which, double2* U, float2* dU,
+                       float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st);
 int launch_unitarity_dev(const double2* E, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
                          const int32_t* bsize, int B, const double* S, const int32_t* us_map, double* part_max,
                          double* part_sum, cudaStream_t st);

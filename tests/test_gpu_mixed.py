@@ -63,6 +63,31 @@ def test_mixed_dipole_and_density(rt, basis, prop):
     assert np.all(obs[:, 9] < 1e-6)
 
 
+@pytest.mark.parametrize("basis", ["spd13", "sp4"])
+def test_mixed_field_polynomial(rt, basis):
+    """FP32 sandwich with the FP64 field-polynomial EM propagator, under a
+    pulse: same bars as the mixed path."""
+    s = synth.diamond_system(2, basis, 6.0, 6.0)
+    K0, _, _ = synth.ground_state_dense(s, 2 * s.n_atoms)
+    steps = 30
+    ctx = rt.RT(s, prop="em", precision="fp32", field_poly=1, **_radii(6.0))
+    ctx.set_field(kind=rt.RT_FIELD_GAUSSIAN, dir=0, E0=5e-3, t0=0.5, sigma=0.3, omega=0.8)
+    ctx.inverse()
+    ctx.set_density_dense(0, 0, K0)
+    ctx.step(steps)
+    obs = ctx.observables(0, 0)
+    ctx.close()
+    ref = oracle.Propagator(s, oracle.Params(prop="em", field={"kind": "gaussian", "E0": 5e-3, "t0": 0.5,
+                                                               "sigma": 0.3, "omega": 0.8}, field_dir=0,
+                                             **_radii(6.0)))
+    ref.set_density_dense(K0)
+    rows = np.array([[z for z in ref.step()["obs"]] for _ in range(steps)])
+    p64 = rows[:, 1].real
+    assert np.abs(obs[:, 3] - p64).max() <= 1e-6 * np.abs(p64).max()
+    q64 = rows[:, 0].real
+    assert np.abs(obs[:, 1] - q64).max() <= 1e-6 * np.abs(q64).max()
+
+
 def test_mixed_unitarity_excess(rt):
     s = synth.diamond_system(2, "spd13", 6.0, 6.0)
     out = {}

@@ -89,12 +89,14 @@ def test_hotelling_matches_oracle(rt, basis, r):
 # --------------------------------------------------------------------------
 
 def _run_pair(rt, s, prop, radii, steps, n_occ, kappa=1e-3, field=None, hot_iters=2, full_step=1,
-              use_graph=1):
+              use_graph=1, field_first=False, **gpu_params):
     K0, _, _ = synth.ground_state_dense(s, n_occ)
     ctx = rt.RT(s, dt=0.05, prop=prop, hot_step_iters=hot_iters, full_step=full_step, use_graph=use_graph,
-                **radii)
+                **radii, **gpu_params)
+    if field and field_first:
+        ctx.set_field(**field)
     ctx.inverse()
-    if field:
+    if field and not field_first:
         ctx.set_field(**field)
     ctx.set_density_dense(0, 0, K0)
     ctx.kick(0, 0, 0, kappa)
@@ -173,6 +175,49 @@ def test_etrs_m4_propagation_step(rt, prop):
     obs, Kg, _, rows, ref = _run_pair(rt, s, prop, _radii(6.0), 6, s.n // 2, field=field, full_step=0)
     assert relerr(Kg, ref.K.val) < REL
     assert relerr(obs[:, 3], rows[:, 3]) < REL
+
+
+@pytest.mark.parametrize("basis,radii", [("sp4", dict(r_Sinv=6.0, r_T=6.0, r_U=7.0, r_K=6.0, r_M=7.0)),
+                                         ("spd13", dict(r_Sinv=6.0, r_T=7.0, r_U=6.0, r_K=6.0, r_M=6.0))])
+@pytest.mark.parametrize("field_first", [False, True])
+def test_field_polynomial_em_matches_oracle(rt, basis, radii, field_first):
+    """EM with U formed as the polynomial sum_m E^m V_m in the field value:
+    the literal truncated series of the oracle, step by step, under a pulse
+    along z (the field axis set after rt_inverse forces the coefficients to
+    be formed again)."""
+    s = synth.diamond_system(2, basis, 6.0, 6.0)
+    field = dict(kind=rt.RT_FIELD_GAUSSIAN, dir=2, E0=5e-3, t0=0.15, sigma=0.1, omega=1.3)
+    obs, Kg, Ug, rows, ref = _run_pair(rt, s, "em", radii, 8, 2 * s.n_atoms, field=field, field_first=field_first,
+                                       field_poly=1)
+    assert relerr(Kg, ref.K.val) < REL
+    assert relerr(Ug, ref.U.val) < REL
+    for col in (1, 3, 5, 7):
+        assert relerr(obs[:, col], rows[:, col]) < REL, col
+    ind_g = obs[:, 7] - obs[0, 7]
+    ind_r = rows[:, 7] - rows[0, 7]
+    assert np.abs(ind_g - ind_r).max() <= 1e-7 * np.abs(ind_r).max()
+
+
+def test_field_polynomial_mixed_blocks_and_terms(rt):
+    """Block sizes 1 and 4 in an open cluster, 7 Taylor terms, kick."""
+    pos, species = synth.si_h_cluster(target=60)
+    s = synth.build_system(pos, None, species, 5.0, 5.0)
+    n_occ = int(np.sum(s.bsize)) // 2
+    K0, _, _ = synth.ground_state_dense(s, n_occ)
+    ctx = rt.RT(s, dt=0.05, field_poly=1, taylor_terms=7, **_radii(7.0))
+    ctx.inverse()
+    ctx.set_density_dense(0, 0, K0)
+    ctx.kick(0, 0, 0, 1e-3)
+    ctx.step(5)
+    obs = ctx.observables(0, 0)
+    Kg = ctx.matrix(0, rt.RT_MAT_K)
+    ctx.close()
+    ref = oracle.Propagator(s, oracle.Params(dt=0.05, taylor_terms=7, **_radii(7.0)))
+    ref.set_density_dense(K0)
+    ref.kick(0, 1e-3)
+    rows = [ref.step()["obs"] for _ in range(5)]
+    assert relerr(Kg, ref.K.val) < REL
+    assert relerr(obs[:, 3], np.array([r[1].real for r in rows])) < REL
 
 
 def test_propagation_step_reuses_u(rt):
