@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--foe-order", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run only the mixed-precision context (FOE ground state, kick, warm-up, steps) and print "
+                         "its per-kernel-class times: a small resident set for kernel captures, no benchmark line")
     ap.add_argument("--study", default=None, choices=["truncation", "scaling"],
                     help="run a study instead of the benchmark and print its JSON line")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NSTEPS",
@@ -147,7 +150,8 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu capture of
 # the same kernel and workload, keyed by (path, kernel class); None when the kernel
 # changed after the capture.
-TRAFFIC = {}
+TRAFFIC = {("diamond 4096 atoms x 13 functions, r_S=r_H=7A, r_Sinv=r_T=r_U=r_K=r_M=8A, dt=0.05, EM 6 terms, "
+            "x-kick 1e-3", "fp32", "gemm_taylor_powers"): 2.785e9 + 1.160e9}  # k_gemm13_r32
 
 
 def derived_alu_peaks(torch, sm_max_mhz):
@@ -394,7 +398,7 @@ def run_gpu(args):
         achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12
         peak = derived[hp]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get((hp, dom)),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get((cfg_name(args), hp, dom)),
                 "peak_source": (f"derived: {derived['sms']} SMs x {'128 FP32 lanes x 2 flops' if hp == 'fp32' else '2 FP64 FMA x 2 flops'}"
                                 f" x {derived['sm_max_ghz']:.3f} GHz"),
                 "cublas_gemm_tflops": {k: round(v, 3) for k, v in peaks.items()},
@@ -719,8 +723,41 @@ def scaling_study(args):
     print(json.dumps(out))
 
 
+def kernel_case(args):
+    """The mixed-precision step alone on the given cell (for ncu captures that must
+    hold only a few GB): FOE ground state, x kick, W warm-up steps, K steps with
+    per-class CUDA-event times."""
+    import torch
+
+    import paper_1404_5776_gb300 as rtm
+    rtm.build()
+    s = workload(args)
+    mu, e_lo, e_hi = model_spectrum(args)
+    R = args.radius
+    ctx = rtm.RT(s, precision="fp32", dt=0.05, prop=args.prop, obs_capacity=args.steps + args.warmup + 8,
+                 r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
+    ctx.inverse()
+    ctx.ground_state(0, args.foe_order, mu, 0.01, e_lo, e_hi)
+    ctx.kick(0, 0, 0, 1e-3)
+    ctx.step(args.warmup)
+    ctx.synchronize()
+    ctx.profile(True)
+    nvtx_push(torch, "timed_kernel_case")
+    ctx.step(args.steps)
+    nvtx_pop(torch)
+    pr = ctx.profile_read()
+    ctx.profile(False)
+    ctx.close()
+    print(json.dumps({"kernel_case": cfg_name(args), "steps": args.steps, "warmup": args.warmup,
+                      "device_mem_gb": round(torch.cuda.max_memory_allocated() / 1e9, 2),
+                      "per_launch_ms": {k: round(v["ms"] / v["launches"], 4) for k, v in pr.items() if v["launches"]}}))
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        kernel_case(args)
+        return
     if args.study == "truncation":
         truncation_study(args)
         return
