@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the mixed-precision context (FOE ground state, kick, warm-up, steps) and print "
                          "its per-kernel-class times: a small resident set for kernel captures, no benchmark line")
-    ap.add_argument("--study", default=None, choices=["truncation", "scaling"],
+    ap.add_argument("--study", default=None, choices=["truncation", "scaling", "batching"],
                     help="run a study instead of the benchmark and print its JSON line")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NSTEPS",
                     help="instead of timing: run both paths NSTEPS steps and report their agreement")
@@ -753,8 +753,103 @@ def kernel_case(args):
                       "per_launch_ms": {k: round(v["ms"] / v["launches"], 4) for k, v in pr.items() if v["launches"]}}))
 
 
+def batching_study(args):
+    """Several systems of uneven size and block size in one context, each with
+    x, y and z kicks, advanced together (one graph per step): diamond cells of
+    512 ... 8000 atoms (13 functions for 512, 1728, 4096, 8000; 4 for 1000,
+    2744, 5832) and the H-terminated Si cluster (4 and 1 functions), r = 8 A.
+    Mixed precision timed over K steps; FP64 over a few steps for the dipole
+    agreement."""
+    import torch
+
+    import synth
+
+    import paper_1404_5776_gb300 as rtm
+    rtm.build()
+    R = args.radius
+    spec = [(4, "spd13"), (5, "sp4"), (6, "spd13"), (7, "sp4"), (8, "spd13"), (9, "sp4"), (10, "spd13")]
+    t0 = time.perf_counter()
+    systems = [synth.diamond_system(nc, b, 7.0, 7.0) for nc, b in spec]
+    pos, species = synth.si_h_cluster(target=1200)
+    systems.append(synth.build_system(pos, None, species, 7.0, 7.0))
+    t_build = time.perf_counter() - t0
+    cl = systems[-1]
+    K0c, _, gap_c = synth.ground_state_dense(cl, int(np.sum(cl.bsize)) // 2)
+    spectra_by_basis = {b: model_spectrum(argparse.Namespace(basis=b)) for b in ("sp4", "spd13")}
+    common = dict(dt=0.05, prop="em", n_kick=3, obs_capacity=args.steps + args.warmup + 16,
+                  r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
+
+    # FP64 context: ground states (FOE; the cluster by dense diagonalisation), x/y/z kicks
+    torch.cuda.reset_peak_memory_stats()
+    c64 = rtm.RT(systems, precision="fp64", **common)
+    c64.inverse()
+    for si, (nc, b) in enumerate(spec):
+        mu, e_lo, e_hi = spectra_by_basis[b]
+        c64.ground_state(si, args.foe_order, mu, 0.01, e_lo, e_hi)
+    for k in range(3):
+        c64.set_density_dense(len(spec), k, K0c)
+    for si in range(len(systems)):
+        for k in range(3):
+            c64.kick(si, k, k, 1e-3)
+    K1 = {(si, k): c64.matrix(si, rtm.RT_MAT_K, k) for si in range(len(systems)) for k in range(3)}
+    # mixed context from the same K(0+)
+    c32 = rtm.RT(systems, precision="fp32", **common)
+    c32.inverse()
+    for (si, k), Kv in K1.items():
+        c32.set_density(si, k, Kv)
+    del K1
+    mem = torch.cuda.max_memory_allocated() / 1e9
+    c32.step(args.warmup)
+    c32.synchronize()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    nvtx_push(torch, "timed_batch_fp32")
+    c32.step(args.steps)
+    nvtx_pop(torch)
+    e1.record()
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1) / args.steps
+    launches = c32.step_kernels()
+    flops, _ = c32.step_work()
+    n64 = 3
+    torch.cuda.synchronize()
+    e0.record()
+    c64.step(n64)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / n64
+    runs = []
+    for si, (nc, b) in enumerate(spec + [(None, "si_h")]):
+        for k in range(3):
+            o64 = c64.observables(si, k)
+            o32 = c32.observables(si, k)[:len(o64)]
+            p64, p32 = o64[:, 3 + 2 * k], o32[:, 3 + 2 * k]
+            ind = np.abs(p64 - p64[0]).max()
+            runs.append({"system": si, "atoms": int(systems[si].n_atoms), "basis": b, "kick": "xyz"[k],
+                         "dipole_err_rel_P": float(np.abs(p32 - p64).max() / np.abs(p64).max()),
+                         "dipole_err_rel_induced": float(np.abs(p32 - p64).max() / ind) if ind > 0 else None})
+    c32.close()
+    c64.close()
+    n_atoms = sum(int(x.n_atoms) for x in systems)
+    out = {"study": "batching", "systems": [{"atoms": int(x.n_atoms), "functions": int(x.n)} for x in systems],
+           "total_atoms": n_atoms, "kicks": 3, "radius_A": R, "steps": args.steps, "warmup": args.warmup,
+           "cluster_gap_Ha": gap_c, "host_build_s": round(t_build, 1),
+           "mixed": {"ms_per_step": round(ms32, 3), "batch_steps_per_s": round(1e3 / ms32, 3),
+                     "atom_kick_steps_per_s": round(3 * n_atoms * 1e3 / ms32, 1),
+                     "algorithmic_tflops": round(flops / ms32 / 1e9, 2), "kernels_per_step": int(launches)},
+           "device_gb_both_contexts": round(mem, 2),
+           "fp64": {"ms_per_step": round(ms64, 1), "timed_steps": n64},
+           "speedup_mixed_vs_fp64": round(ms64 / ms32, 2),
+           "dipole_agreement_over_fp64_steps": runs}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.study == "batching":
+        batching_study(args)
+        return
     if args.kernel_case:
         kernel_case(args)
         return

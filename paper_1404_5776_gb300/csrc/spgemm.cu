@@ -352,6 +352,7 @@ static void dispatch_prec(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const
 }
 
 bool launch_gemm13_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const GemmArgs& g, cudaStream_t st);
+bool launch_gemm4_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const GemmArgs& g, cudaStream_t st);
 
 void launch_gemm(int B, bool fp32, bool cplx, bool a_dag, bool b_dag, Epilogue epi, const GemmArgs& g,
                  cudaStream_t st) {
@@ -360,6 +361,7 @@ void launch_gemm(int B, bool fp32, bool cplx, bool a_dag, bool b_dag, Epilogue e
     if (launch_gemm13_f32(cplx, a_dag, b_dag, epi, g, st)) return;
     throw Error{RT_EINTERNAL, "FP32 13-function product variant has no kernel"};
   }
+  if (B == 4 && fp32 && launch_gemm4_f32(cplx, a_dag, b_dag, epi, g, st)) return;
   switch (B) {
     case 1: return fp32 ? dispatch_prec<1, float>(cplx, a_dag, b_dag, epi, g, st)
                         : dispatch_prec<1, double>(cplx, a_dag, b_dag, epi, g, st);
