@@ -33,7 +33,13 @@ constexpr int BS = 13;
 constexpr int NE = BS * BS;
 constexpr int RS = 16;        // padded row stride
 constexpr int SB = BS * RS;   // padded block (elements)
-constexpr int WARPS = 4;
+// Pipeline shape per kernel: warps per CTA and stages per warp (a stage holds
+// NT staged triples; S stages keep S - 1 groups in flight while one is used).
+constexpr int WARPS = 4;         // complex kernel
+constexpr int C_STAGES = 2;
+constexpr int R_WARPS = 4;       // real kernel
+constexpr int R_STAGES = 2;
+constexpr int MAX_STAGES = 4;
 // One staged triple = A block + B block + 16 bytes of skew, so that the lane
 // groups' broadcast reads of different triples fall on different banks.
 template <typename V>
@@ -120,19 +126,29 @@ __device__ __forceinline__ int group_block(const int2* __restrict__ ab, int64_t 
 }
 
 struct Smem {
-  uint64_t bar[WARPS][2];
+  uint64_t bar[8][MAX_STAGES];  // [warp][stage]
 };
+static_assert(WARPS <= 8 && R_WARPS <= 8 && C_STAGES <= MAX_STAGES && R_STAGES <= MAX_STAGES, "pipeline shape");
+static_assert(sizeof(Smem) <= 256, "control block");
+
+// dynamic shared memory per CTA (control block + every warp's stages) and the
+// CTAs per SM it leaves room for (227 KB per SM for CTAs)
+constexpr size_t SMEM_C = 256 + (size_t)WARPS * C_STAGES * (2 * Slot<float2>::STRIDE) * sizeof(float2);  // NT = 2
+constexpr size_t SMEM_R = 256 + (size_t)R_WARPS * R_STAGES * (4 * Slot<float>::STRIDE) * sizeof(float);  // NT = 4
+constexpr int MINB_C = (int)((227 * 1024) / (SMEM_C + 1024));
+constexpr int MINB_R = (int)((227 * 1024) / (SMEM_R + 1024));
+static_assert(MINB_C >= 1 && MINB_R >= 1, "stages do not fit in shared memory");
 
 // Elements of a 13 x 13 block handled by one lane in the per-element epilogues.
 constexpr int EPT = (NE + 31) / 32;
 
 // ---------------------------------------------------------------------------
 // Main loop shared by both kernels: stream the item's triples through the
-// warp's two stages, NT triples per stage (lane group h takes slot h), and
-// call `mac(sA, sB)` on each staged pair.  Returns false if a wait expired
-// (copies in flight have then been drained, bounded).
+// warp's S stages, NT triples per stage (lane group h takes slot h), S - 1
+// groups in flight, and call `mac(sA, sB)` on each staged pair.  Returns
+// false if a wait expired (copies in flight have then been drained, bounded).
 // ---------------------------------------------------------------------------
-template <typename V, int NT, typename F>
+template <typename V, int NT, int S, typename F>
 __device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* __restrict__ A,
                                                const V* __restrict__ B, const V* __restrict__ Z,
                                                const int2* __restrict__ ab, int64_t t0, int64_t t1, int lane,
@@ -140,22 +156,32 @@ __device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* _
   constexpr int WBUF = NT * Slot<V>::STRIDE;
   unsigned phase = 0u;    // bit s: parity to wait for on stage s
   unsigned pending = 0u;  // bit s: copies in flight into stage s
-  int stage = 0;
-  int nblk = -1;  // this lane's block index for the next group (prefetched)
-  if (t0 < t1) {
-    issue_group<V, NT>(wsm, A, B, group_block<NT>(ab, t0, t1, lane), Z, &bar[0], lane);
-    nblk = group_block<NT>(ab, t0 + NT, t1, lane);
-    pending |= 1u;
+  int64_t tnext = t0;     // first triple of the next group to issue
+  int snext = 0;          // the stage it goes into
+  int blk = group_block<NT>(ab, t0, t1, lane);  // this lane's block index for that group
+#pragma unroll
+  for (int k = 0; k < S - 1; ++k) {
+    if (tnext < t1) {
+      issue_group<V, NT>(wsm + snext * WBUF, A, B, blk, Z, &bar[snext], lane);
+      pending |= 1u << snext;
+      tnext += NT;
+      snext = snext + 1 == S ? 0 : snext + 1;
+      blk = group_block<NT>(ab, tnext, t1, lane);
+    }
   }
+  int stage = 0;
   for (int64_t tb = t0; tb < t1; tb += NT) {
-    if (tb + NT < t1) {
-      issue_group<V, NT>(wsm + (stage ^ 1) * WBUF, A, B, nblk, Z, &bar[stage ^ 1], lane);
-      nblk = group_block<NT>(ab, tb + 2 * NT, t1, lane);  // used one iteration later
-      pending |= 1u << (stage ^ 1);
+    if (tnext < t1) {
+      // refill the stage used in the previous iteration (released by its __syncwarp)
+      issue_group<V, NT>(wsm + snext * WBUF, A, B, blk, Z, &bar[snext], lane);
+      pending |= 1u << snext;
+      tnext += NT;
+      snext = snext + 1 == S ? 0 : snext + 1;
+      blk = group_block<NT>(ab, tnext, t1, lane);  // used one iteration later
     }
     if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
       // bounded drain of every stage with copies in flight (this one included)
-      for (int st = 0; st < 2; ++st)
+      for (int st = 0; st < S; ++st)
         if ((pending >> st) & 1u) mbar_wait(&bar[st], (phase >> st) & 1u);
       return false;
     }
@@ -164,7 +190,7 @@ __device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* _
     const V* sA = wsm + stage * WBUF + h * Slot<V>::STRIDE;
     mac(sA, sA + SB);
     __syncwarp();  // all lanes done with this stage before it is refilled
-    stage ^= 1;
+    stage = stage + 1 == S ? 0 : stage + 1;
   }
   return true;
 }
@@ -176,7 +202,7 @@ __device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* _
 // 169 elements of the block with all 32 lanes.
 // ---------------------------------------------------------------------------
 template <int EPI>
-__global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
+__global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
   constexpr int NT = 2;
   constexpr int WBUF = NT * Slot<float2>::STRIDE;  // one stage of one warp (float2)
   const int lane = threadIdx.x & 31;
@@ -186,12 +212,11 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
   const int64_t item = (int64_t)blockIdx.x * WARPS + warp;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   Smem* ctl = reinterpret_cast<Smem*>(dyn_smem);
-  float2* wsm = reinterpret_cast<float2*>(dyn_smem + 128) + (size_t)warp * 2 * WBUF;
+  float2* wsm = reinterpret_cast<float2*>(dyn_smem + 256) + (size_t)warp * C_STAGES * WBUF;
   if (item >= g.n_items) return;  // whole warp leaves together
   uint64_t* bar = ctl->bar[warp];
   if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int st = 0; st < C_STAGES; ++st) mbar_init(&bar[st], 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -200,7 +225,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
 #pragma unroll
   for (int r = 0; r < BS; ++r) acc[r] = make_float2(0.f, 0.f);
 
-  const bool ok = stream_triples<float2, NT>(
+  const bool ok = stream_triples<float2, NT, C_STAGES>(
       wsm, bar, static_cast<const float2*>(g.A), static_cast<const float2*>(g.B),
       static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h,
       [&](const float2* sA, const float2* sB) {
@@ -383,7 +408,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_c32(GemmArgs g) {
 // epilogue scheme as above.
 // ---------------------------------------------------------------------------
 template <int EPI>
-__global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_r32(GemmArgs g) {
+__global__ void __launch_bounds__(R_WARPS * 32, MINB_R) k_gemm13_r32(GemmArgs g) {
   constexpr int NT = 4;
   constexpr int RH = 7;  // rows per half
   constexpr int WBUF = NT * Slot<float>::STRIDE;
@@ -393,15 +418,14 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_r32(GemmArgs g) {
   const int half = (lane >> 2) & 1;
   const int cl = lane & 3;
   const int r0 = RH * half;
-  const int64_t item = (int64_t)blockIdx.x * WARPS + warp;
+  const int64_t item = (int64_t)blockIdx.x * R_WARPS + warp;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   Smem* ctl = reinterpret_cast<Smem*>(dyn_smem);
-  float* wsm = reinterpret_cast<float*>(dyn_smem + 128) + (size_t)warp * 2 * WBUF;
+  float* wsm = reinterpret_cast<float*>(dyn_smem + 256) + (size_t)warp * R_STAGES * WBUF;
   if (item >= g.n_items) return;
   uint64_t* bar = ctl->bar[warp];
   if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int st = 0; st < R_STAGES; ++st) mbar_init(&bar[st], 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -410,7 +434,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_gemm13_r32(GemmArgs g) {
 #pragma unroll
   for (int rr = 0; rr < RH; ++rr) acc[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  const bool ok = stream_triples<float, NT>(
+  const bool ok = stream_triples<float, NT, R_STAGES>(
       wsm, bar, static_cast<const float*>(g.A), static_cast<const float*>(g.B), static_cast<const float*>(g.zero),
       g.ab, g.ptr[item], g.ptr[item + 1], lane, h, [&](const float* sA, const float* sB) {
         float4 b[BS];  // B[m][4cl .. 4cl+3]
@@ -512,10 +536,10 @@ bool launch_gemm13_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const Ge
   if (a_dag || b_dag) return false;
   if (g.n_items == 0) return true;
   RT_REQUIRE(g.zero != nullptr, RT_EINTERNAL, "FP32 products need a zero block");
-  int64_t grid = (g.n_items + WARPS - 1) / WARPS;
-  RT_REQUIRE(grid < (1ll << 31), RT_EINTERNAL, "grid too large");
-  const size_t smem_c = 128 + (size_t)WARPS * 2 * (2 * Slot<float2>::STRIDE) * sizeof(float2);  // 2 stages x NT=2
-  const size_t smem_r = 128 + (size_t)WARPS * 2 * (4 * Slot<float>::STRIDE) * sizeof(float);    // 2 stages x NT=4
+  const int64_t grid_c = (g.n_items + WARPS - 1) / WARPS;
+  const int64_t grid_r = (g.n_items + R_WARPS - 1) / R_WARPS;
+  RT_REQUIRE(grid_c < (1ll << 31), RT_EINTERNAL, "grid too large");
+  const size_t smem_c = SMEM_C, smem_r = SMEM_R;
   static bool attr_done = false;
   if (!attr_done) {
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
@@ -526,13 +550,13 @@ bool launch_gemm13_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const Ge
     attr_done = true;
   }
   if (cplx) {
-    if (epi == EPI_STORE) k_gemm13_c32<EPI_STORE><<<(unsigned)grid, WARPS * 32, smem_c, st>>>(g);
-    else if (epi == EPI_ADD) k_gemm13_c32<EPI_ADD><<<(unsigned)grid, WARPS * 32, smem_c, st>>>(g);
-    else if (epi == EPI_DELTA_SANDWICH) k_gemm13_c32<EPI_DELTA_SANDWICH><<<(unsigned)grid, WARPS * 32, smem_c, st>>>(g);
+    if (epi == EPI_STORE) k_gemm13_c32<EPI_STORE><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+    else if (epi == EPI_ADD) k_gemm13_c32<EPI_ADD><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+    else if (epi == EPI_DELTA_SANDWICH) k_gemm13_c32<EPI_DELTA_SANDWICH><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
     else return false;
   } else {
-    if (epi == EPI_STORE) k_gemm13_r32<EPI_STORE><<<(unsigned)grid, WARPS * 32, smem_r, st>>>(g);
-    else if (epi == EPI_STORE_ACC) k_gemm13_r32<EPI_STORE_ACC><<<(unsigned)grid, WARPS * 32, smem_r, st>>>(g);
+    if (epi == EPI_STORE) k_gemm13_r32<EPI_STORE><<<(unsigned)grid_r, R_WARPS * 32, smem_r, st>>>(g);
+    else if (epi == EPI_STORE_ACC) k_gemm13_r32<EPI_STORE_ACC><<<(unsigned)grid_r, R_WARPS * 32, smem_r, st>>>(g);
     else return false;
   }
   RT_CUDA_CHECK(cudaGetLastError());
