@@ -38,7 +38,9 @@
  *     that return data to the host synchronise that stream.
  *   - Every call returns an rt_status; rt_last_error(ctx) gives the reason of the
  *     last failure.  After RT_ECUDA, RT_ETIMEOUT or RT_EINTERNAL the context is
- *     poisoned: every later call except rt_last_error/rt_destroy returns RT_ESTATE.
+ *     poisoned: every later call except rt_last_error, rt_set_state and
+ *     rt_destroy returns RT_ESTATE; rt_set_state (a checkpoint of this context)
+ *     clears the poisoned state and the device error word.
  *   - Device memory comes from the allocator passed to rt_create (cudaMalloc
  *     when it is NULL) and is owned by the context until rt_destroy.
  */
@@ -301,6 +303,25 @@ RT_API rt_status rt_traces_noalloc(const double* K, int64_t nnzb, const int32_t*
 
 /* Waits for all work of the context's stream. */
 RT_API rt_status rt_synchronize(rt_ctx* ctx);
+
+/* Host-side fault injection for tests (no counterpart in the paper; nothing
+ * is made to fault or hang on the GPU).  Flags (or-ed):
+ *   RT_FAULT_HOTELLING_MAXITER1  the next rt_inverse runs with hot_maxit = 1,
+ *                                so it ends with RT_ENOTCONV;
+ *   RT_FAULT_NAN_IN_H            writes a NaN into the first element of H0 of
+ *                                system 0 (and of the precomputed S^-1 H0 of
+ *                                the FP32 EM mode, if formed): the next step's
+ *                                observables are NaN and rt_observables returns
+ *                                RT_ENUMERIC.  Permanent for this context;
+ *   RT_FAULT_WAIT_TIMEOUT_0      the next rt_step gives its bounded waits
+ *                                (FP32 13-function kernels) a zero budget: they
+ *                                give up at once, drain the copies in flight and
+ *                                set the error word, and the step returns
+ *                                RT_ETIMEOUT; the context is then refused
+ *                                (RT_ESTATE) until rt_set_state.
+ * Errors: RT_EINVAL for unknown flags. */
+enum { RT_FAULT_HOTELLING_MAXITER1 = 1, RT_FAULT_NAN_IN_H = 2, RT_FAULT_WAIT_TIMEOUT_0 = 4 };
+RT_API rt_status rt_debug_inject(rt_ctx* ctx, uint32_t flags);
 
 /* Reason of the last failure (never NULL; "" after success). */
 RT_API const char* rt_last_error(rt_ctx* ctx);

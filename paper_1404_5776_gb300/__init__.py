@@ -23,6 +23,7 @@ from . import _build
 # constants (mirror include/rt.h)
 # ----------------------------------------------------------------------------
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ENUMERIC, RT_ETIMEOUT, RT_EINTERNAL, RT_ESTATE = range(9)
+RT_FAULT_HOTELLING_MAXITER1, RT_FAULT_NAN_IN_H, RT_FAULT_WAIT_TIMEOUT_0 = 1, 2, 4
 STATUS_NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV", 5: "RT_ENUMERIC",
                 6: "RT_ETIMEOUT", 7: "RT_EINTERNAL", 8: "RT_ESTATE"}
 RT_PROP_EM, RT_PROP_CN, RT_PROP_ETRS, RT_PROP_M4 = 0, 1, 2, 3
@@ -37,7 +38,8 @@ OBS_FIELDS = ["t", "trks_re", "trks_im", "trkdx_re", "trkdx_im", "trkdy_re", "tr
 EXPORTED = ["rt_default_params", "rt_create", "rt_set_field", "rt_inverse", "rt_set_density", "rt_ground_state",
             "rt_kick", "rt_propagator", "rt_step", "rt_observables", "rt_pattern_size", "rt_get_pattern",
             "rt_matrix_size", "rt_get_matrix", "rt_unitarity", "rt_step_work", "rt_step_kernels", "rt_profile", "rt_profile_read",
-            "rt_get_state", "rt_set_state", "rt_synchronize", "rt_last_error", "rt_destroy", "rt_traces_noalloc"]
+            "rt_get_state", "rt_set_state", "rt_synchronize", "rt_last_error", "rt_destroy", "rt_traces_noalloc",
+            "rt_debug_inject"]
 
 
 class rt_system(ctypes.Structure):
@@ -107,6 +109,7 @@ def load(path: Optional[str] = None):
         "rt_get_state": [P, P, P],
         "rt_set_state": [P, P, ctypes.c_size_t],
         "rt_synchronize": [P],
+        "rt_debug_inject": [P, ctypes.c_uint32],
         "rt_traces_noalloc": [P, I64, P, P, P, I32, P, P, P, P, P, P, I32, P, P],
     }
     for name, args in sig.items():
@@ -366,6 +369,10 @@ class RT:
 
     def synchronize(self):
         self._c(self.lib.rt_synchronize(self.ctx))
+
+    def debug_inject(self, flags: int):
+        """Host-side fault injection (RT_FAULT_* flags) for tests."""
+        self._c(self.lib.rt_debug_inject(self.ctx, flags))
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <memory>
 #include <tuple>
@@ -114,6 +115,8 @@ struct rt_ctx {
   rt::DevState* dstate = nullptr;
   void* zero32 = nullptr;  // one zero FP32 complex block (padded layout)
   int* d_err = nullptr;    // device error word of bounded waits
+  long long wait_ns = 2000000000ll;  // budget of one bounded device wait
+  uint32_t inject = 0;     // armed host-side fault injections (RT_FAULT_*)
   double* ring = nullptr;  // [capacity][n_slots][RT_NOBS]
   int n_slots = 0;
   int64_t host_step = 0;  // steps enqueued since the last time reset
@@ -273,6 +276,7 @@ static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cpl
   g.bsize = s.d_bsize;
   g.zero = c->zero32;
   g.err = c->d_err;
+  g.wait_ns = c->wait_ns;
   int B = s.B;
   run(c, cls, gemm_flops(ti, cplx), gemm_bytes(s, ti, cplx, fp32),
       [&] { launch_gemm(B, fp32, cplx, ad, bd, epi, g, c->ws); });
@@ -1286,14 +1290,26 @@ rt_status rt_inverse(rt_ctx* c, int32_t sys, int32_t* iters, double* residual) {
   return guarded(c, [&] {
     if (sys >= 0) check_sys(c, sys);
     rt_status worst = RT_OK;
+    const int32_t maxit = c->p.hot_maxit;
+    if (c->inject & RT_FAULT_HOTELLING_MAXITER1) {
+      c->p.hot_maxit = 1;
+      c->inject &= ~(uint32_t)RT_FAULT_HOTELLING_MAXITER1;
+    }
     for (size_t i = 0; i < c->sys.size(); ++i) {
-      rt_status st = hotelling_sinv(c, *c->sys[i]);
+      rt_status st = RT_OK;
+      try {
+        st = hotelling_sinv(c, *c->sys[i]);
+      } catch (...) {
+        c->p.hot_maxit = maxit;
+        throw;
+      }
       if (st != RT_OK) {
         worst = st;
         c->err = "Hotelling " + c->sys[i]->sinv_status + " for system " + std::to_string(i) +
                  " (residual " + std::to_string(c->sys[i]->sinv_resid) + ")";
       }
     }
+    c->p.hot_maxit = maxit;
     int32_t k = sys >= 0 ? sys : 0;
     if (iters) *iters = c->sys[k]->sinv_iters;
     if (residual) *residual = c->sys[k]->sinv_resid;
@@ -1409,6 +1425,26 @@ rt_status rt_step(rt_ctx* c, int32_t n) {
       for (auto& sp : c->sys)
         for (int k = 0; k < c->p.n_kick; ++k)
           if (!sp->ref_fresh[k]) make_reference(c, *sp, k);
+    }
+    if (c->inject & RT_FAULT_WAIT_TIMEOUT_0) {
+      // one step, launched directly, with a zero wait budget; the error word
+      // is read back here so that this call reports the expiry
+      c->inject &= ~(uint32_t)RT_FAULT_WAIT_TIMEOUT_0;
+      c->wait_ns = 0;
+      try {
+        enqueue_step(c);
+      } catch (...) {
+        c->wait_ns = 2000000000ll;
+        throw;
+      }
+      c->wait_ns = 2000000000ll;
+      c->graph_dirty = true;
+      c->host_step += 1;
+      c->t_host += c->p.dt;
+      RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+      check_device_error(c);
+      if (n == 1) return RT_OK;
+      --n;
     }
     if (c->profiling || !c->p.use_graph) {
       for (int i = 0; i < n; ++i) enqueue_step(c);
@@ -1714,7 +1750,26 @@ rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
     }
     c->host_step = h.host_step;
     c->t_host = h.t_host;
+    RT_CUDA_CHECK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->ws));  // the restored state is sound again
+    c->graph_dirty = true;
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    return RT_OK;
+  });
+}
+
+rt_status rt_debug_inject(rt_ctx* c, uint32_t flags) {
+  return guarded(c, [&] {
+    const uint32_t known = RT_FAULT_HOTELLING_MAXITER1 | RT_FAULT_NAN_IN_H | RT_FAULT_WAIT_TIMEOUT_0;
+    RT_REQUIRE((flags & ~known) == 0, RT_EINVAL, "unknown fault flags");
+    if (flags & RT_FAULT_NAN_IN_H) {
+      Sys& s = *c->sys[0];
+      const double nan = std::numeric_limits<double>::quiet_NaN();
+      RT_CUDA_CHECK(cudaMemcpyAsync(s.H0, &nan, sizeof(double), cudaMemcpyHostToDevice, c->ws));
+      if (s.T0) RT_CUDA_CHECK(cudaMemcpyAsync(s.T0, &nan, sizeof(double), cudaMemcpyHostToDevice, c->ws));
+      if (!s.V.empty()) RT_CUDA_CHECK(cudaMemcpyAsync(s.V[0], &nan, sizeof(double), cudaMemcpyHostToDevice, c->ws));
+      RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    }
+    c->inject |= flags & (RT_FAULT_HOTELLING_MAXITER1 | RT_FAULT_WAIT_TIMEOUT_0);
     return RT_OK;
   });
 }

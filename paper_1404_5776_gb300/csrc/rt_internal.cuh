@@ -152,6 +152,7 @@ struct GemmArgs {
   const void* addend3;      // incremental form: FP32 M_lo through add_map (FP32 block layout) or null
   const void* zero;         // a zero block (FP32 kernels stage it for missing triples)
   int* err;                 // device error word (bounded waits that gave up)
+  long long wait_ns;        // budget of one bounded wait (FP32 kernels), nanoseconds
 };
 
 // Row stride of an FP32 block: 13-function blocks are padded to 13 x 16

@@ -21,7 +21,8 @@
 //     written contiguously);
 //   * B^dagger operands are pre-transposed (a conjugate-transposed copy of
 //     U - I), so every staged block is a straight copy;
-//   * every wait on an mbarrier is bounded: on expiry the kernel records an
+//   * every wait on an mbarrier is bounded in time (the launch's budget, 2 s
+//     by default, read from the global timer): on expiry the kernel records an
 //     error code, waits (bounded) for its copies in flight and returns.
 #include "rt_internal.cuh"
 
@@ -47,7 +48,7 @@ struct Slot {
   static constexpr int SKEW = 16 / sizeof(V);
   static constexpr int STRIDE = 2 * SB + SKEW;  // elements
 };
-constexpr long long SPIN_LIMIT = 1ll << 26;  // ~ seconds of polling before giving up
+constexpr long long DRAIN_NS = 2000000000ll;  // budget of the drain after a wait gave up (2 s)
 
 __device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 c) {
   c.x = fmaf(a.x, b.x, c.x);
@@ -80,17 +81,31 @@ __device__ __forceinline__ void tma_load_1d(void* sdst, const void* gsrc, unsign
       "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// bounded wait for the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  unsigned addr = smem_u32(bar);
-  for (long long it = 0; it < SPIN_LIMIT; ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
+__device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity, at most budget_ns nanoseconds of
+// the global timer (and at most 2^30 polls); false on expiry.  A budget of 0
+// gives up at once (host-side fault injection of a wait that expires).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long budget_ns) {
+  if (budget_ns <= 0) return false;
+  const unsigned addr = smem_u32(bar);
+  if (mbar_try(addr, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1; it < (1u << 30); ++it) {
+    if (mbar_try(addr, parity)) return true;
+    if ((it & 63u) == 0u && (long long)(global_ns() - t0) > budget_ns) return false;
   }
   return false;
 }
@@ -152,7 +167,7 @@ template <typename V, int NT, int S, typename F>
 __device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* __restrict__ A,
                                                const V* __restrict__ B, const V* __restrict__ Z,
                                                const int2* __restrict__ ab, int64_t t0, int64_t t1, int lane,
-                                               int h, F&& mac) {
+                                               int h, long long wait_ns, F&& mac) {
   constexpr int WBUF = NT * Slot<V>::STRIDE;
   unsigned phase = 0u;    // bit s: parity to wait for on stage s
   unsigned pending = 0u;  // bit s: copies in flight into stage s
@@ -179,10 +194,11 @@ __device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* _
       snext = snext + 1 == S ? 0 : snext + 1;
       blk = group_block<NT>(ab, tnext, t1, lane);  // used one iteration later
     }
-    if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) {
-      // bounded drain of every stage with copies in flight (this one included)
+    if (!mbar_wait(&bar[stage], (phase >> stage) & 1u, wait_ns)) {
+      // bounded drain of every stage with copies in flight (this one included):
+      // no copy may still be landing in shared memory when the warp leaves
       for (int st = 0; st < S; ++st)
-        if ((pending >> st) & 1u) mbar_wait(&bar[st], (phase >> st) & 1u);
+        if ((pending >> st) & 1u) mbar_wait(&bar[st], (phase >> st) & 1u, DRAIN_NS);
       return false;
     }
     phase ^= 1u << stage;
@@ -227,7 +243,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
 
   const bool ok = stream_triples<float2, NT, C_STAGES>(
       wsm, bar, static_cast<const float2*>(g.A), static_cast<const float2*>(g.B),
-      static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h,
+      static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns,
       [&](const float2* sA, const float2* sB) {
         float2 bcol[BS];
 #pragma unroll
@@ -436,7 +452,7 @@ __global__ void __launch_bounds__(R_WARPS * 32, MINB_R) k_gemm13_r32(GemmArgs g)
 
   const bool ok = stream_triples<float, NT, R_STAGES>(
       wsm, bar, static_cast<const float*>(g.A), static_cast<const float*>(g.B), static_cast<const float*>(g.zero),
-      g.ab, g.ptr[item], g.ptr[item + 1], lane, h, [&](const float* sA, const float* sB) {
+      g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns, [&](const float* sA, const float* sB) {
         float4 b[BS];  // B[m][4cl .. 4cl+3]
 #pragma unroll
         for (int m = 0; m < BS; ++m) b[m] = *reinterpret_cast<const float4*>(sB + m * RS + 4 * cl);
