@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the mixed-precision context (FOE ground state, kick, warm-up, steps) and print "
                          "its per-kernel-class times: a small resident set for kernel captures, no benchmark line")
-    ap.add_argument("--study", default=None, choices=["truncation", "scaling", "batching"],
+    ap.add_argument("--study", default=None, choices=["truncation", "scaling", "batching", "propagators"],
                     help="run a study instead of the benchmark and print its JSON line")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NSTEPS",
                     help="instead of timing: run both paths NSTEPS steps and report their agreement")
@@ -845,8 +845,69 @@ def batching_study(args):
     print(json.dumps(out))
 
 
+def propagators_study(args):
+    """EM, ETRS, M4 and CN (Sec. II.A) under a Gaussian pulse on a 512-atom cell
+    (13 functions, r = 8 A): dipole error against an M4 run at dt/8, charge
+    drift, S-unitarity of the last U and time per step, for several dt, FP64
+    and mixed."""
+    import torch
+
+    import synth
+
+    import paper_1404_5776_gb300 as rtm
+    rtm.build()
+    s = synth.diamond_system(4, "spd13", 7.0, 7.0)
+    K0, _, gap = synth.ground_state_dense(s, 2 * s.n_atoms)
+    R = 8.0
+    radii = dict(r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
+    t_end = 4.0
+    field = dict(kind=rtm.RT_FIELD_GAUSSIAN, dir=0, E0=5e-3, t0=1.0, sigma=0.3, omega=0.6)
+
+    def run(prop, dt, precision="fp64"):
+        n = int(round(t_end / dt))
+        ctx = rtm.RT(s, dt=dt, prop=prop, precision=precision, obs_capacity=n + 8, **radii)
+        ctx.set_field(**field)
+        ctx.inverse()
+        ctx.set_density_dense(0, 0, K0)
+        ctx.step(2)  # warm-up (graph capture), then restart from K0
+        ctx.set_density_dense(0, 0, K0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.step(n)
+        e1.record()
+        torch.cuda.synchronize()
+        obs = ctx.observables(0, 0)
+        u = ctx.unitarity(0, True)
+        ctx.close()
+        return obs, e0.elapsed_time(e1) / n, u
+
+    ref_obs, _, _ = run("m4", 0.05 / 8)
+    t_ref = ref_obs[:, 0]
+    p_ref = ref_obs[:, 3]
+    recs = []
+    for dt in (0.05, 0.1, 0.2):
+        for prop in ("em", "etrs", "m4", "cn"):
+            for precision in ("fp64", "fp32"):
+                obs, ms, u = run(prop, dt, precision)
+                idx = np.searchsorted(t_ref, obs[:, 0] - 1e-9)
+                ok = idx < len(t_ref)
+                err = np.abs(obs[ok, 3] - p_ref[idx[ok]]).max()
+                swing = np.abs(p_ref - p_ref[0]).max()
+                recs.append({"prop": prop, "dt": dt, "precision": precision, "ms_per_step": round(ms, 3),
+                             "dipole_err_vs_ref_rel_swing": float(err / swing),
+                             "charge_drift_rel": float(np.abs(obs[:, 1] - obs[0, 1]).max() / abs(obs[0, 1])),
+                             "unitarity_max": u[0]})
+    print(json.dumps({"study": "propagators", "system": f"{s.n_atoms} atoms x 13, r = 8 A, gap {gap:.3f} Ha",
+                      "field": "gaussian E0 5e-3, t0 1.0, sigma 0.3, omega 0.6, along x", "t_end": t_end,
+                      "reference": "M4 at dt = 0.05/8, FP64", "runs": recs}))
+
+
 def main():
     args = parse()
+    if args.study == "propagators":
+        propagators_study(args)
+        return
     if args.study == "batching":
         batching_study(args)
         return

@@ -132,7 +132,8 @@ typedef struct {
   int32_t prop;             /* RT_PROP_EM (paper, default), RT_PROP_CN, RT_PROP_ETRS
                                or RT_PROP_M4 (both Sec. II.A); ETRS and M4 build
                                U in FP64 in either precision                      */
-  int32_t taylor_terms;     /* EM: terms of the exponential series in total (6)  */
+  int32_t taylor_terms;     /* terms of every exponential series in total (EM,
+                               ETRS, M4; 6 in the paper), 1..32                  */
   double hot_tol;           /* Hotelling tolerance on ||I - S X||_F / sqrt(n)     */
   int32_t hot_maxit;        /* Hotelling iteration cap for rt_inverse             */
   int32_t hot_step_iters;   /* CN: Hotelling iterations per step                  */
