@@ -1325,6 +1325,15 @@ rt_status rt_set_density(rt_ctx* c, int32_t sys, int32_t kick, const double* h) 
     Sys& s = *c->sys[sys];
     const Pattern& P = *s.pK;
     const int B = s.B;
+    if (!s.ref_fresh.empty()) s.ref_fresh[kick] = 0;  // K replaced: the incremental reference is void
+    if (s.n_true == (int64_t)s.n_atoms * B) {
+      // no padded atoms: the caller's layout is the device layout; copy directly
+      // (a DMA at full speed when the caller's buffer is pinned)
+      RT_CUDA_CHECK(cudaMemcpyAsync(s.K[kick], h, sizeof(double2) * nvals(s, s.pK), cudaMemcpyHostToDevice, c->ws));
+      reset_time(c);
+      RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+      return RT_OK;
+    }
     std::vector<double> buf(2 * (size_t)P.nnzb * B * B, 0.0);
     size_t o = 0;
     for (int i = 0; i < s.n_atoms; ++i)
@@ -1339,7 +1348,6 @@ rt_status rt_set_density(rt_ctx* c, int32_t sys, int32_t kick, const double* h) 
           }
         o += (size_t)bi * bj;
       }
-    if (!s.ref_fresh.empty()) s.ref_fresh[kick] = 0;  // K replaced: the incremental reference is void
     RT_CUDA_CHECK(cudaMemcpyAsync(s.K[kick], buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->ws));
     reset_time(c);
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
