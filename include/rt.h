@@ -82,7 +82,9 @@ enum { RT_FIELD_NONE = 0, RT_FIELD_GAUSSIAN = 1, RT_FIELD_CONSTANT = 2 };
 enum {
   RT_MAT_S = 0, RT_MAT_H0 = 1, RT_MAT_DX = 2, RT_MAT_DY = 3, RT_MAT_DZ = 4,
   RT_MAT_SINV = 5, /* Hotelling S^-1 on P_Sinv                             */
-  RT_MAT_T = 6,    /* last T = S^-1 H(t+dt/2) on P_T (EM)                  */
+  RT_MAT_T = 6,    /* last T = cut(S^-1 H) on P_T formed by a step: EM at
+                      t+dt/2, ETRS at t+dt, M4 at t1 (not formed per step by
+                      the field polynomial)                                */
   RT_MAT_U = 7,    /* last propagator on P_U                               */
   RT_MAT_K = 8,    /* density matrix of (sys, kick) on P_K                 */
   RT_MAT_X = 9     /* CN warm-start inverse (S + i dt/2 H)^-1 on P_U       */
@@ -214,8 +216,10 @@ RT_API rt_status rt_ground_state(rt_ctx* ctx, int32_t sys, int32_t order, double
  * powers cut to r_U. Needs rt_inverse. */
 RT_API rt_status rt_kick(rt_ctx* ctx, int32_t sys, int32_t kick, int32_t dir, double kappa);
 
-/* Builds U for [t, t+dt] for every system (eq. EM at the midpoint, or the CN
- * form) and keeps it for steps with full_step = 0. */
+/* Builds U for [t, t+dt] for every system with the context's propagator
+ * (EM at the midpoint, its field polynomial, ETRS, M4 or the CN form) and
+ * keeps it for steps with full_step = 0 (in the incremental form also as FP32
+ * hi + lo parts).  Synchronises. */
 RT_API rt_status rt_propagator(rt_ctx* ctx, double t);
 
 /* n time steps K <- U K U^dagger for every (system, kick), each followed by the
@@ -264,8 +268,10 @@ RT_API rt_status rt_profile(rt_ctx* ctx, int32_t enable);
 RT_API rt_status rt_profile_read(rt_ctx* ctx, int32_t max, int32_t* n_classes, int64_t* launches,
                           double* ms, double* flops, double* bytes, char* names /* [max][32] */);
 
-/* Checkpoint: every K, the CN warm start, time, step counter.  With buf NULL,
- * *bytes receives the size.  rt_set_state restores it (and clears poisoning). */
+/* Checkpoint: every K, U, the CN warm start, the device step state (time,
+ * field samples), the step counter and the observables cursor.  With buf
+ * NULL, *bytes receives the size.  rt_set_state restores it (and clears the
+ * poisoned state and the device error word). */
 RT_API rt_status rt_get_state(rt_ctx* ctx, void* buf, size_t* bytes);
 RT_API rt_status rt_set_state(rt_ctx* ctx, const void* buf, size_t bytes);
 
