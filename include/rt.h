@@ -163,6 +163,12 @@ typedef struct {
                                to rounding, in FP64 in either precision; holds
                                (taylor_terms + 1) complex FP64 matrices on P_U and
                                twice that many real ones while they are formed  */
+  int32_t hot_fp64_iters;   /* CN with RT_FP32: how many of the hot_step_iters
+                               iterations of each step (the last ones, with the
+                               reported residual) run in FP64; the earlier ones
+                               run as FP32 block products (Hotelling converges
+                               quadratically: an FP64 iteration squares the FP32
+                               error away).  1..hot_step_iters; default 1       */
 } rt_params;
 
 typedef struct {
@@ -173,7 +179,8 @@ typedef struct {
 
 /* Fills the defaults: radii 8 A, dt 0.05, EM, 6 Taylor terms, tol 1e-10,
  * maxit 100, 2 CN iterations per step, FP64, full step, 1 kick, 12 kick terms,
- * 4096 observable steps, graphs on, incremental form and field polynomial off. */
+ * 4096 observable steps, graphs on, incremental form and field polynomial off,
+ * 1 FP64 CN iteration per step in the mixed mode. */
 RT_API rt_status rt_default_params(rt_params* p);
 
 /* Creates a context for n_sys systems: validates and copies the host inputs,

@@ -798,4 +798,55 @@ void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// FP32 Hotelling iterations of the CN propagator (mixed mode)
+// ---------------------------------------------------------------------------
+// Y <- 2I - Y on P_U, FP32 complex in the FP32 block layout (in place)
+__global__ void k_two_i_minus32(float2* __restrict__ Y, int64_t nnzb, const int32_t* __restrict__ rowidx,
+                                const int32_t* __restrict__ col, int B, int rs) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = idx / NE;
+    const int e = (int)(idx - q * NE);
+    const int r = e / B, c = e - r * B;
+    const int64_t o = q * (int64_t)B * rs + r * rs + c;
+    const float d = (rowidx[q] == col[q] && r == c) ? 2.f : 0.f;
+    const float2 y = Y[o];
+    Y[o] = make_float2(d - y.x, -y.y);
+  }
+}
+
+void launch_two_i_minus32(float2* Y, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B,
+                          cudaStream_t st) {
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_two_i_minus32<<<(unsigned)g, 256, 0, st>>>(Y, nnzb, rowidx, col, B, rs32(B));
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// FP32 complex blocks (FP32 block layout) to FP64 complex dense blocks
+__global__ void k_f2d_unpad(const float2* __restrict__ a, double2* __restrict__ b, int64_t nnzb, int B, int rs) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t NE = (int64_t)B * B;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = idx / NE;
+    const int e = (int)(idx - q * NE);
+    const int r = e / B, c = e - r * B;
+    const float2 v = a[q * (int64_t)B * rs + r * rs + c];
+    b[idx] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+void launch_f2d_unpad(const float2* a, double2* b, int64_t nnzb, int B, cudaStream_t st) {
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_f2d_unpad<<<(unsigned)g, 256, 0, st>>>(a, b, nnzb, B, rs32(B));
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
 }  // namespace rt

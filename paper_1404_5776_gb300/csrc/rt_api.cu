@@ -80,6 +80,8 @@ struct Sys {
   // FP32 buffers (mixed precision)
   float *Tf = nullptr, *Pf0 = nullptr, *Pf1 = nullptr;
   float2 *dUf = nullptr, *dUH = nullptr, *Kf = nullptr, *Mf = nullptr, *Wf = nullptr;
+  // FP32 Hotelling iterations of the mixed CN step: A on P_A, X, Y = A X (then 2I - A X), X Y on P_U
+  float2 *Acn32 = nullptr, *X32 = nullptr, *Y32 = nullptr, *Xn32 = nullptr;
   // incremental form (FP32, constant U): K = K_ref + dK, R = U K_ref U^dagger - K_ref
   std::vector<double2*> Kref, dK, Rm;
   std::vector<double*> tref;      // reference traces (8 doubles per kick)
@@ -466,6 +468,15 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
     RT_CUDA_CHECK(cudaMemsetAsync(s.Kf, 0, sizeof(float2) * nvals32(s, s.pK), c->ws));
     RT_CUDA_CHECK(cudaMemsetAsync(s.Mf, 0, sizeof(float2) * nvals32(s, s.pM), c->ws));
     RT_CUDA_CHECK(cudaMemsetAsync(s.Wf, 0, sizeof(float2) * nvals32(s, s.pM), c->ws));
+    if (p.prop == RT_PROP_CN && p.hot_step_iters > p.hot_fp64_iters) {
+      s.Acn32 = c->arena.get_n<float2>(nvals32(s, s.pA));
+      s.X32 = c->arena.get_n<float2>(nvals32(s, s.pU));
+      s.Y32 = c->arena.get_n<float2>(nvals32(s, s.pU));
+      s.Xn32 = c->arena.get_n<float2>(nvals32(s, s.pU));
+      for (float2* b : {s.X32, s.Y32, s.Xn32})  // padding columns stay zero
+        RT_CUDA_CHECK(cudaMemsetAsync(b, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Acn32, 0, sizeof(float2) * nvals32(s, s.pA), c->ws));
+    }
     if (p.prop == RT_PROP_EM) {
       s.Tf = c->arena.get_n<float>(nvals32(s, s.pT));
       s.Pf0 = c->arena.get_n<float>(nvals32(s, s.pU));
@@ -805,19 +816,44 @@ static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
     TripleInfo& tAX = triples_for(c, s, s.pA, false, s.pU, false, s.pU, false);
     TripleInfo& tXZ = triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);
     TripleInfo& tXB = triples_for(c, s, s.pU, false, s.pA, false, s.pU, false);
+    // mixed mode: the first iterations as FP32 block products (X rounded to
+    // FP32 and back); the last hot_fp64_iters in FP64, with the residual
+    const int n32 = (fp32 && s.X32) ? std::max(0, p.hot_step_iters - p.hot_fp64_iters) : 0;
+    if (n32 > 0) {
+      run(
+          c, PC_MISC, 0, 0,
+          [&] {
+            launch_d2f_pad(reinterpret_cast<const double*>(s.Acn), reinterpret_cast<float*>(s.Acn32), s.pA->nnzb,
+                           s.B, true, c->ws);
+            launch_d2f_pad(reinterpret_cast<const double*>(s.X), reinterpret_cast<float*>(s.X32), s.pU->nnzb, s.B,
+                           true, c->ws);
+          },
+          2);
+      float2* x32[2] = {s.X32, s.Xn32};
+      for (int it = 0; it < n32; ++it) {
+        float2* xi = x32[it % 2];
+        float2* xo = x32[(it + 1) % 2];
+        gemm(c, s, PC_CN_HOT, tAX, true, true, false, false, EPI_STORE, args(s.Acn32, xi, s.Y32), s.pU);
+        run(c, PC_MISC, 0, 0,
+            [&] { launch_two_i_minus32(s.Y32, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws); });
+        gemm(c, s, PC_CN_HOT, tXZ, true, true, false, false, EPI_STORE, args(xi, s.Y32, xo), s.pU);
+      }
+      run(c, PC_MISC, 0, 0, [&] { launch_f2d_unpad(x32[n32 % 2], s.X, s.pU->nnzb, s.B, c->ws); });
+    }
     // X alternates between two fixed buffers and ends in s.X, so that a
     // captured step graph can be replayed (no host-side pointer swaps)
+    const int n64 = p.hot_step_iters - n32;
     double2* xb[2] = {s.X, s.Xn};
-    for (int it = 0; it < p.hot_step_iters; ++it) {
+    for (int it = 0; it < n64; ++it) {
       double2* xi = xb[it % 2];
       double2* xo = xb[(it + 1) % 2];
       GemmArgs g = args(s.Acn, xi, s.Zc);
       g.red = s.red_items;
       gemm(c, s, PC_CN_HOT, tAX, false, true, false, false, EPI_TWO_I, g, s.pU);
-      if (it == p.hot_step_iters - 1) residual_from_items(c, s, tAX, s.scal + 1, nullptr);
+      if (it == n64 - 1) residual_from_items(c, s, tAX, s.scal + 1, nullptr);
       gemm(c, s, PC_CN_HOT, tXZ, false, true, false, false, EPI_STORE, args(xi, s.Zc, xo), s.pU);
     }
-    if (p.hot_step_iters % 2 == 1)
+    if (n64 % 2 == 1)
       run(c, PC_MISC, 0, 0, [&] {
         RT_CUDA_CHECK(cudaMemcpyAsync(s.X, s.Xn, sizeof(double2) * nvals(s, s.pU), cudaMemcpyDeviceToDevice, c->ws));
       });
@@ -1183,6 +1219,7 @@ rt_status rt_default_params(rt_params* p) {
   p->hot_tol = 1e-10;
   p->hot_maxit = 100;
   p->hot_step_iters = 2;
+  p->hot_fp64_iters = 1;
   p->precision = RT_FP64;
   p->full_step = 1;
   p->n_kick = 1;
@@ -1215,6 +1252,8 @@ rt_status rt_create(rt_ctx** out, const rt_system* sys, int32_t n_sys, const rt_
     RT_REQUIRE(q.n_kick >= 1 && q.n_kick <= 3, RT_EINVAL, "n_kick must be in 1..3");
     RT_REQUIRE(q.obs_capacity >= 1, RT_EINVAL, "obs_capacity must be positive");
     RT_REQUIRE(q.hot_step_iters >= 0 && q.hot_maxit >= 0 && q.kick_terms >= 1, RT_EINVAL, "bad iteration counts");
+    RT_REQUIRE(q.hot_step_iters == 0 || (q.hot_fp64_iters >= 1 && q.hot_fp64_iters <= q.hot_step_iters), RT_EINVAL,
+               "hot_fp64_iters must be in 1..hot_step_iters");
     RT_REQUIRE((int64_t)n_sys * q.n_kick <= RT_MAX_SLOTS, RT_EINVAL, "too many (system, kick) pairs");
     RT_REQUIRE(!q.incremental || (q.precision == RT_FP32 && !q.full_step), RT_EINVAL,
                "the incremental form needs precision RT_FP32 and full_step = 0");

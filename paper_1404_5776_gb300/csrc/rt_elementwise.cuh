@@ -77,6 +77,11 @@ void launch_symmetrise_to_complex(const double* Kr, double2* K, int64_t nnzb, co
                                   cudaStream_t st);
 void launch_d2f_pad(const double* a, float* b, int64_t nnzb, int B, bool cplx, cudaStream_t st);
 void launch_dagger32(const float2* dU, float2* dUH, int64_t nnzb, int B, cudaStream_t st);
+// Y <- 2I - Y (FP32 complex, FP32 block layout, in place; identity on diagonal blocks)
+void launch_two_i_minus32(float2* Y, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B,
+                          cudaStream_t st);
+// FP32 complex (FP32 block layout) -> FP64 complex dense blocks
+void launch_f2d_unpad(const float2* a, double2* b, int64_t nnzb, int B, cudaStream_t st);
 void launch_delta_w(const double2* K, const int32_t* m_to_k, const float2* Mf, float2* Wf, int64_t nnzb_m, int B,
                     cudaStream_t st);
 void launch_set_hot(DevState* s, const double* resid, int iters, cudaStream_t st);
