@@ -103,3 +103,20 @@ def test_zero_kick_ground_state_is_stationary(rt):
     assert relerr(obs[:, 3], rows[:, 1]) < 1e-10
     # stationary up to the truncation of U (P_U misses one block pair per row)
     assert np.abs(obs[:, 3] - obs[0, 3]).max() < 1e-4 * abs(obs[0, 3])
+
+
+def test_cn_fp64_iteration_count_validated(rt):
+    s = synth.diamond_system(2, "sp4", 6.0, 6.0)
+    for bad in (0, 3):
+        with pytest.raises(rt.RTError) as e:
+            rt.RT(s, prop="cn", precision="fp32", hot_step_iters=2, hot_fp64_iters=bad)
+        assert e.value.status == rt.RT_EINVAL
+
+
+def test_cn_all_fp64_iterations_match_oracle_in_mixed_mode(rt):
+    """hot_fp64_iters = hot_step_iters: the mixed CN path with every Hotelling
+    iteration in FP64 (only the sandwich in FP32)."""
+    s = synth.diamond_system(2, "spd13", 6.0, 6.0)
+    radii = dict(r_Sinv=6.0, r_T=6.0, r_U=6.0, r_K=6.0, r_M=6.0)
+    obs, Kg, rows, ref = _pair(rt, s, radii, 6, "fp32", prop="cn", hot_fp64_iters=2)
+    assert relerr(obs[:, 3], rows[:, 1]) < 1e-6
