@@ -85,7 +85,8 @@ enum {
   RT_MAT_T = 6,    /* last T = cut(S^-1 H) on P_T formed by a step: EM at
                       t+dt/2, ETRS at t+dt, M4 at t1 (not formed per step by
                       the field polynomial)                                */
-  RT_MAT_U = 7,    /* last propagator on P_U                               */
+  RT_MAT_U = 7,    /* last propagator on P_U (the FP32 EM mode holds U - I in
+                      FP32; it is returned as I + (U - I))                 */
   RT_MAT_K = 8,    /* density matrix of (sys, kick) on P_K                 */
   RT_MAT_X = 9     /* CN warm-start inverse (S + i dt/2 H)^-1 on P_U       */
 };

@@ -98,6 +98,7 @@ struct Sys {
   double* rows_tmp = nullptr;
   bool sinv_ready = false;
   bool u_ready = false;
+  bool duf_current = false;  // the FP32 EM mode's U - I holds the last propagator (U itself is not formed)
   int sinv_iters = 0;
   double sinv_resid = 0.0;
   std::string sinv_status;
@@ -790,6 +791,7 @@ static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
       launch_field_poly(V, deg, c->dstate, E_MID, fp32 ? nullptr : s.U, fp32 ? s.dUf : nullptr,
                         fp32 ? s.dUH : nullptr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
     });
+    s.duf_current = fp32;
     return;
   }
   if (p.prop == RT_PROP_EM) {
@@ -798,6 +800,7 @@ static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
       run(c, PC_FIELD, 0, 16.0 * nvals(s, s.pT),
           [&] { launch_field_axpy(s.T0, s.TD, c->dstate, E_MID, 1.0, s.T, (int64_t)nvals(s, s.pT), c->ws); });
       taylor_series(c, s, s.T, p.dt, p.taylor_terms, true);
+      s.duf_current = true;
     } else {
       field_T(c, s, E_MID, s.T);
       taylor_series(c, s, s.T, p.dt, p.taylor_terms, false);
@@ -1023,6 +1026,7 @@ static void kick_one(rt_ctx* c, Sys& s, int kick, int dir, double kappa) {
   gemm(c, s, PC_MISC, tM, false, true, false, false, EPI_STORE, args(s.U, s.K[kick], s.M), s.pM);
   gemm(c, s, PC_MISC, tK, false, true, false, true, EPI_SANDWICH, args(s.M, s.U, s.K[kick]), s.pK);
   s.u_ready = false;  // U now holds V
+  s.duf_current = false;
 }
 
 // K0 = f(S^-1 H0) S^-1 by a Chebyshev expansion (real FP64 on P_K)
@@ -1604,6 +1608,8 @@ rt_status rt_get_matrix(rt_ctx* c, int32_t sys, int32_t kick, int32_t which, dou
     const void* v;
     bool cplx;
     if (which == RT_MAT_K) materialize(c, s);
+    if (which == RT_MAT_U && s.duf_current)
+      launch_u_from_delta(s.dUf, s.U, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);  // U = I + (U - I)
     matrix_by_id(c, s, kick, which, &P, &v, &cplx);
     RT_REQUIRE(vals, RT_EINVAL, "NULL output");
     int64_t need = 2 * true_elems(s, P);
