@@ -1,0 +1,138 @@
+"""Pins (CPU, FP64) for the algebraic reformulations the CUDA path uses on top
+of the paper's step, each restated here with the oracle's truncated products
+and compared with the literal computation:
+
+* T(E) = cut(S^-1 (H0 - E D)) = cut(S^-1 H0) - E cut(S^-1 D)    (the FP32 EM path)
+* delta-form sandwich: with dU = U - I, M = cut_M(dU K), W = K + M,
+  K' = K + M + cut_K(W dU^dagger)  equals  cut_K(cut_M(U K) U^dagger)   (r_M >= r_K)
+* incremental form: sandwich(K_ref + dK) = K_ref + R + dK + M + N with
+  R = sandwich(K_ref) - K_ref, M = cut(dU dK), N = cut((dK + M) dU^dagger)
+* field polynomial: U(E) = sum_m E^m V_m with V_m = sum_n c_n Q_{n,m},
+  Q_{1,0} = T0, Q_{1,1} = -T_D, Q_{n,m} = cut(T0 Q_{n-1,m}) + cut(Q_{1,1} Q_{n-1,m-1}),
+  equals the literal truncated series of T(E) at every E.
+The hermitian mirroring of K' (upper blocks computed, lower mirrored) is the
+same on both sides and is applied to both."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+@pytest.fixture(scope="module")
+def setup():
+    s = synth.diamond_system(2, "sp4", 6.0, 6.0)
+    pats = {r: oracle.pattern(s.pos, s.cell, r) for r in (4.0, 5.0, 6.0, 7.0)}
+    S = oracle.BlockMatrix(s.bsize, oracle.Pattern(s.s_rowptr, s.s_col), s.s_val)
+    hp = oracle.Pattern(s.h_rowptr, s.h_col)
+    H0 = oracle.BlockMatrix(s.bsize, hp, s.h_val)
+    D = oracle.BlockMatrix(s.bsize, hp, s.d_val[0])
+    Sinv = oracle.hotelling(S, pats[6.0], 1e-12, 100).X
+    K0, _, _ = synth.ground_state_dense(s, s.n // 2)
+    return s, pats, S, H0, D, Sinv, K0
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def test_T_is_linear_in_the_field(setup):
+    s, pats, S, H0, D, Sinv, _ = setup
+    pT = pats[5.0]
+    T0 = oracle.spgemm(Sinv, H0, pT)
+    TD = oracle.spgemm(Sinv, D, pT)
+    for E in (1e-3, -0.05):
+        TE = oracle.spgemm(Sinv, oracle.hamiltonian(H0, D, E), pT)
+        assert rel(TE.val, T0.val - E * TD.val) < 1e-13
+
+
+def _sandwich_direct(U, K, pM, pK):
+    Kn, _ = oracle.sandwich(U, K, pM)
+    assert Kn.pat is pK or np.array_equal(Kn.pat.col, pK.col)
+    return Kn
+
+
+def _delta_sandwich(dU, K, pM, pK):
+    M = oracle.spgemm(dU, K, pM)
+    W = oracle.axpy(1.0, K, M)                      # K + M on P_M
+    Kn = oracle.axpy(1.0, M, K.copy())              # K + M on P_K
+    oracle.spgemm(W, dU, pK, b_dag=True, upper_only=True, out=(X := oracle.zeros(K.bsize, pK)))
+    up = oracle.BlockMatrix(K.bsize, pK, Kn.val + X.val, Kn.voff)
+    oracle.mirror_upper(up)
+    return up
+
+
+def _propagator(setup, r_T, r_U, dt=0.05, terms=6):
+    s, pats, S, H0, D, Sinv, _ = setup
+    T = oracle.spgemm(Sinv, H0, pats[r_T])
+    U, _ = oracle.taylor_em(T, dt, terms, pats[r_U])
+    return U
+
+
+@pytest.mark.parametrize("r_K,r_M", [(5.0, 5.0), (5.0, 7.0), (6.0, 6.0)])
+def test_delta_form_equals_direct_sandwich(setup, r_K, r_M):
+    s, pats, *_ , K0 = setup
+    U = _propagator(setup, 5.0, 6.0)
+    pK, pM = pats[r_K], pats[r_M]
+    K = oracle.from_dense(s.bsize, pK, K0.astype(complex))
+    dU = oracle.axpy(-1.0, oracle.identity(s.bsize, U.pat), U)
+    direct = _sandwich_direct(U, K, pM, pK)
+    delta = _delta_sandwich(dU, K, pM, pK)
+    assert rel(delta.val, direct.val) < 1e-13
+
+
+def test_incremental_form_equals_direct_sandwich(setup):
+    s, pats, *_, K0 = setup
+    U = _propagator(setup, 5.0, 6.0)
+    pK = pM = pats[6.0]
+    dU = oracle.axpy(-1.0, oracle.identity(s.bsize, U.pat), U)
+    K_ref = oracle.from_dense(s.bsize, pK, K0.astype(complex))
+    rng = np.random.default_rng(3)
+    dK = oracle.BlockMatrix(s.bsize, pK, 1e-3 * (rng.standard_normal(K_ref.val.shape)
+                                                 + 1j * rng.standard_normal(K_ref.val.shape)))
+    oracle.mirror_upper(dK)  # hermitian perturbation
+    K = oracle.axpy(1.0, dK, K_ref.copy())
+    direct = _sandwich_direct(U, K, pM, pK)
+    R = oracle.axpy(-1.0, K_ref, _sandwich_direct(U, K_ref, pM, pK))
+    d_new = _delta_sandwich(dU, dK, pM, pK)          # dK + M + N
+    incr = oracle.axpy(1.0, R, oracle.axpy(1.0, K_ref, d_new))
+    assert rel(incr.val, direct.val) < 1e-13
+
+
+@pytest.mark.parametrize("terms", [2, 6, 7])
+def test_field_polynomial_equals_literal_series(setup, terms):
+    s, pats, S, H0, D, Sinv, _ = setup
+    pT, pU = pats[4.0], pats[6.0]
+    dt = 0.05
+    T0 = oracle.spgemm(Sinv, H0, pT)
+    Q1 = [T0, oracle.BlockMatrix(s.bsize, pT, -oracle.spgemm(Sinv, D, pT).val)]
+    deg = terms - 1
+    V = [oracle.identity(s.bsize, pU)] + [oracle.zeros(s.bsize, pU) for _ in range(deg)]
+
+    def coef(n):
+        return (-1j * dt) ** n / math.factorial(n)
+
+    for m in range(min(deg, 1) + 1):
+        if deg >= 1:
+            V[m] = oracle.axpy(coef(1), oracle.restrict(Q1[m], pU), V[m])
+    prev = Q1
+    for n in range(2, deg + 1):
+        cur = []
+        for m in range(n + 1):
+            acc = oracle.zeros(s.bsize, pU)
+            if m <= n - 1:
+                acc = oracle.axpy(1.0, oracle.spgemm(Q1[0], prev[m], pU), acc)
+            if m >= 1:
+                acc = oracle.axpy(1.0, oracle.spgemm(Q1[1], prev[m - 1], pU), acc)
+            cur.append(acc)
+            V[m] = oracle.axpy(coef(n), acc, V[m])
+        prev = cur
+    for E in (0.0, 2e-3, -0.03):
+        poly = V[deg].val.copy()
+        for m in range(deg - 1, -1, -1):
+            poly = poly * E + V[m].val
+        TE = oracle.spgemm(Sinv, oracle.hamiltonian(H0, D, E), pT)
+        U_lit, _ = oracle.taylor_em(TE, dt, terms, pU)
+        assert rel(poly, U_lit.val) < 1e-12, (terms, E)
