@@ -7,8 +7,8 @@
  *
  * Two plain routines, written for obviousness rather than speed:
  *
- *  or_pattern_*  : spatial cut-off of Sec. II.A ("beyond this cut-off radius
- *                  the matrix elements are set to zero").  Block (i,j) is kept
+ *  or_pattern_*  : spatial cut-off of Sec. II.A (elements between atoms
+ *                  farther apart than the radius are dropped).  Block (i,j) is kept
  *                  iff the minimum-image distance of atoms i and j is strictly
  *                  below r.  Brute force over all pairs, FP64, every operation
  *                  separately rounded (compiled with -ffp-contract=off):
