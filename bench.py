@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the mixed-precision context (FOE ground state, kick, warm-up, steps) and print "
                          "its per-kernel-class times: a small resident set for kernel captures, no benchmark line")
-    ap.add_argument("--study", default=None, choices=["truncation", "scaling", "batching", "propagators"],
+    ap.add_argument("--study", default=None, choices=["truncation", "scaling", "batching", "propagators",
+                                                       "propagator-timing"],
                     help="run a study instead of the benchmark and print its JSON line")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NSTEPS",
                     help="instead of timing: run both paths NSTEPS steps and report their agreement")
@@ -855,11 +856,12 @@ def batching_study(args):
     print(json.dumps(out))
 
 
-def propagators_study(args):
+def propagators_study(args, timing_only=False):
     """EM, ETRS, M4 and CN (Sec. II.A) under a Gaussian pulse on a 512-atom cell
     (13 functions, r = 8 A): dipole error against an M4 run at dt/8, charge
     drift, S-unitarity of the last U and time per step, for several dt, FP64
-    and mixed."""
+    and mixed.  timing_only: time per step of each propagator over the first
+    20 steps (dt = 0.05), FP64 and mixed, and their dipole difference."""
     import torch
 
     import synth
@@ -874,7 +876,7 @@ def propagators_study(args):
     field = dict(kind=rtm.RT_FIELD_GAUSSIAN, dir=0, E0=5e-3, t0=1.0, sigma=0.3, omega=0.6)
 
     def run(prop, dt, precision="fp64"):
-        n = int(round(t_end / dt))
+        n = int(round((1.0 if timing_only else t_end) / dt))
         ctx = rtm.RT(s, dt=dt, prop=prop, precision=precision, obs_capacity=n + 8, **radii)
         ctx.set_field(**field)
         ctx.inverse()
@@ -892,6 +894,23 @@ def propagators_study(args):
         ctx.close()
         return obs, e0.elapsed_time(e1) / n, u
 
+    if timing_only:
+        # time per step of every propagator, FP64 and mixed, over the first
+        # 20 steps of the same run (dt = 0.05), and the mixed run's dipole
+        # against the FP64 run of the same propagator
+        recs = []
+        for prop in ("em", "etrs", "m4", "cn"):
+            o64, ms64, u64 = run(prop, 0.05, "fp64")
+            o32, ms32, u32 = run(prop, 0.05, "fp32")
+            recs.append({"prop": prop, "ms_per_step_fp64": round(ms64, 3), "ms_per_step_mixed": round(ms32, 3),
+                         "speedup": round(ms64 / ms32, 2),
+                         "dipole_mixed_vs_fp64_rel_P": float(np.abs(o32[:, 3] - o64[:, 3]).max()
+                                                             / np.abs(o64[:, 3]).max()),
+                         "unitarity_max_fp64": u64[0], "unitarity_max_mixed": u32[0]})
+        print(json.dumps({"study": "propagator-timing", "system": f"{s.n_atoms} atoms x 13, r = 8 A",
+                          "field": "gaussian E0 5e-3, t0 1.0, sigma 0.3, omega 0.6, along x",
+                          "dt": 0.05, "steps": 20, "runs": recs}))
+        return
     ref_obs, _, _ = run("m4", 0.05 / 8)
     t_ref = ref_obs[:, 0]
     p_ref = ref_obs[:, 3]
@@ -915,8 +934,8 @@ def propagators_study(args):
 
 def main():
     args = parse()
-    if args.study == "propagators":
-        propagators_study(args)
+    if args.study in ("propagators", "propagator-timing"):
+        propagators_study(args, timing_only=args.study == "propagator-timing")
         return
     if args.study == "batching":
         batching_study(args)

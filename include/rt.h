@@ -85,8 +85,8 @@ enum {
   RT_MAT_T = 6,    /* last T = cut(S^-1 H) on P_T formed by a step: EM at
                       t+dt/2, ETRS at t+dt, M4 at t1 (not formed per step by
                       the field polynomial)                                */
-  RT_MAT_U = 7,    /* last propagator on P_U (the FP32 EM mode holds U - I in
-                      FP32; it is returned as I + (U - I))                 */
+  RT_MAT_U = 7,    /* last propagator on P_U (the FP32 EM, ETRS and M4 modes
+                      hold U - I in FP32; it is returned as I + (U - I))   */
   RT_MAT_K = 8,    /* density matrix of (sys, kick) on P_K                 */
   RT_MAT_X = 9     /* CN warm-start inverse (S + i dt/2 H)^-1 on P_U       */
 };
@@ -141,7 +141,10 @@ typedef struct {
   int32_t hot_maxit;        /* Hotelling iteration cap for rt_inverse             */
   int32_t hot_step_iters;   /* CN: Hotelling iterations per step                  */
   int32_t precision;        /* RT_FP64 or RT_FP32 (block products in FP32, K,
-                               reductions and the last CN iteration in FP64)     */
+                               reductions and the last CN iteration in FP64;
+                               EM, ETRS and M4 build U - I in FP32 from
+                               T(t) = S^-1 H0 - E(t) S^-1 D, both cut to r_T
+                               and formed once in FP64)                          */
   int32_t full_step;        /* 1: rebuild U for every step; 0: reuse U            */
   int32_t n_kick;           /* density matrices per system sharing U (1..3)       */
   int32_t kick_terms;       /* Taylor terms of the kick exponential               */
@@ -255,8 +258,9 @@ RT_API rt_status rt_get_matrix(rt_ctx* ctx, int32_t sys, int32_t kick, int32_t w
  * with metric_S = 1, E = cut_{P_U}(U^dagger cut_{P_W}(S U)) - S (the conserved
  * form in a non-orthogonal basis); with 0, E = cut_{P_U}(U^dagger U) - I (the
  * printed form).  Host outputs max|E| and mean|E| over the entries of P_U.
- * In the FP32 EM mode the propagator is held as U - I in FP32; it is promoted
- * to U = I + (U - I) in FP64 first, so E measures the mixed propagator. */
+ * In the FP32 EM, ETRS and M4 modes the propagator is held as U - I in FP32;
+ * it is promoted to U = I + (U - I) in FP64 first, so E measures the mixed
+ * propagator. */
 RT_API rt_status rt_unitarity(rt_ctx* ctx, int32_t sys, int32_t metric_S, double* maxabs, double* meanabs);
 
 /* Algorithmic work of one step summed over systems and kicks:
@@ -325,7 +329,7 @@ RT_API rt_status rt_synchronize(rt_ctx* ctx);
  *                                so it ends with RT_ENOTCONV;
  *   RT_FAULT_NAN_IN_H            writes a NaN into the first element of H0 of
  *                                system 0 (and of the precomputed S^-1 H0 of
- *                                the FP32 EM mode, if formed): the next step's
+ *                                the FP32 EM, ETRS and M4 modes, if formed): the next step's
  *                                observables are NaN and rt_observables returns
  *                                RT_ENUMERIC.  Permanent for this context;
  *   RT_FAULT_WAIT_TIMEOUT_0      the next rt_step gives its bounded waits

@@ -735,6 +735,62 @@ void launch_zaxpy(double2* z, const double2* x, const double2* y, double a, int6
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
+// z = x + a y (FP32 complex, element by element; FP32 block layout with its
+// zero padding columns, which stay zero)
+__global__ void k_axpy32(float2* __restrict__ z, const float2* __restrict__ x, const float2* __restrict__ y, float a,
+                         int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 xv = x[i], yv = y[i];
+    z[i] = make_float2(fmaf(a, yv.x, xv.x), fmaf(a, yv.y, xv.y));
+  }
+}
+
+void launch_axpy32(float2* z, const float2* x, const float2* y, float a, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_axpy32<<<(unsigned)g, 256, 0, st>>>(z, x, y, a, n);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// Mixed-mode M4 exponent on P_U in the FP32 block layout:
+// Om = -i dt/2 (T1 + T2) - (sqrt(3) dt^2/12) (C21 - C12), the field part from
+// the FP64 T1, T2 on P_T (through u_to_t), the commutator from the FP32
+// products C21 = cut(T2 T1), C12 = cut(T1 T2); dU = Om as the first term of
+// exp(Om) - I (zero when the series has only its identity term).
+__global__ void k_m4_omega32(const double* __restrict__ T1, const double* __restrict__ T2,
+                             const int32_t* __restrict__ u_to_t, const float* __restrict__ C21,
+                             const float* __restrict__ C12, double dt, float2* __restrict__ Om,
+                             float2* __restrict__ dU, int first_term, int64_t nnzb_u, int B, int rs) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int NE = B * B;
+  const double cc = sqrt(3.0) * dt * dt / 12.0;
+  for (; idx < nnzb_u * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = idx / NE;
+    const int e = (int)(idx - q * NE);
+    const int r = e / B, c = e - r * B;
+    const int tq = u_to_t ? u_to_t[q] : (int)q;
+    double ts = 0.0;
+    if (tq >= 0) ts = T1[(int64_t)tq * NE + e] + T2[(int64_t)tq * NE + e];
+    const int64_t pidx = q * (int64_t)B * rs + r * rs + c;
+    const float2 om = make_float2((float)(-cc * ((double)C21[pidx] - (double)C12[pidx])), (float)(-0.5 * dt * ts));
+    Om[pidx] = om;
+    dU[pidx] = first_term ? om : make_float2(0.f, 0.f);
+  }
+}
+
+void launch_m4_omega32(const double* T1, const double* T2, const int32_t* u_to_t, const float* C21, const float* C12,
+                       double dt, float2* Om, float2* dU, bool first_term, int64_t nnzb_u, int B, cudaStream_t st) {
+  int64_t n = nnzb_u * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_m4_omega32<<<(unsigned)g, 256, 0, st>>>(T1, T2, u_to_t, C21, C12, dt, Om, dU, first_term ? 1 : 0, nnzb_u, B,
+                                            rs32(B));
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------------------
 // field polynomial of the EM propagator
 // ---------------------------------------------------------------------------

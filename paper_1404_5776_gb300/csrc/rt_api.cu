@@ -80,6 +80,10 @@ struct Sys {
   // FP32 buffers (mixed precision)
   float *Tf = nullptr, *Pf0 = nullptr, *Pf1 = nullptr;
   float2 *dUf = nullptr, *dUH = nullptr, *Kf = nullptr, *Mf = nullptr, *Wf = nullptr;
+  // FP32 ETRS: the two half-step differences exp(-i dt/2 T) - I; FP32 M4:
+  // the powers of Om (dUa, dUb), Om itself and T2 in FP32
+  float2 *dUa = nullptr, *dUb = nullptr, *Omf = nullptr;
+  float* Tf2 = nullptr;
   // FP32 Hotelling iterations of the mixed CN step: A on P_A, X, Y = A X (then 2I - A X), X Y on P_U
   float2 *Acn32 = nullptr, *X32 = nullptr, *Y32 = nullptr, *Xn32 = nullptr;
   // incremental form (FP32, constant U): K = K_ref + dK, R = U K_ref U^dagger - K_ref
@@ -478,7 +482,19 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
         RT_CUDA_CHECK(cudaMemsetAsync(b, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
       RT_CUDA_CHECK(cudaMemsetAsync(s.Acn32, 0, sizeof(float2) * nvals32(s, s.pA), c->ws));
     }
-    if (p.prop == RT_PROP_EM) {
+    if (p.prop == RT_PROP_ETRS || p.prop == RT_PROP_M4) {
+      s.dUa = c->arena.get_n<float2>(nvals32(s, s.pU));
+      s.dUb = c->arena.get_n<float2>(nvals32(s, s.pU));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.dUa, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.dUb, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+    }
+    if (p.prop == RT_PROP_M4) {
+      s.Omf = c->arena.get_n<float2>(nvals32(s, s.pU));
+      s.Tf2 = c->arena.get_n<float>(nvals32(s, s.pT));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Omf, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Tf2, 0, sizeof(float) * nvals32(s, s.pT), c->ws));
+    }
+    if (p.prop != RT_PROP_CN) {
       s.Tf = c->arena.get_n<float>(nvals32(s, s.pT));
       s.Pf0 = c->arena.get_n<float>(nvals32(s, s.pU));
       s.Pf1 = c->arena.get_n<float>(nvals32(s, s.pU));
@@ -578,7 +594,7 @@ static rt_status hotelling_sinv(rt_ctx* c, Sys& s) {
   s.sinv_resid = res;
   s.sinv_ready = true;
   if (s.X) launch_restrict(s.Sinv, (double*)s.X, s.u_to_sinv, s.pU->nnzb, s.B, 1, c->ws);
-  if (c->p.precision == RT_FP32 && c->p.prop == RT_PROP_EM) {
+  if (c->p.precision == RT_FP32 && c->p.prop != RT_PROP_CN) {
     // T0 = cut(S^-1 H0) and T_D = cut(S^-1 D_dir): T(t) = T0 - E(t) T_D exactly
     TripleInfo& tT = triples_for(c, s, P, false, s.pH, false, s.pT, false);
     gemm(c, s, PC_MISC, tT, false, false, false, false, EPI_STORE, args(s.Sinv, s.H0, s.T0), s.pT);
@@ -606,10 +622,13 @@ static void taylor_coef(int n, double dt, double* mag, int* imag) {
 }
 
 // U = sum_{n<terms} c_n T^n with T real on P_T, powers cut to P_U.  FP64 U
-// (into Uout, default s.U) or the FP32 difference dU = U - I.
+// (into Uout, default s.U) or the FP32 difference dU = U - I (into dUout;
+// by default s.dUf, with (U - I)^dagger into s.dUH where that exists).
 static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int terms, bool fp32_delta,
-                          double2* Uout = nullptr) {
+                          double2* Uout = nullptr, float2* dUout = nullptr) {
   if (!Uout) Uout = s.U;
+  float2* dUH = dUout ? nullptr : s.dUH;
+  if (!dUout) dUout = s.dUf;
   TripleInfo& t2 = triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);
   TripleInfo& tn = triples_for(c, s, s.pT, false, s.pU, false, s.pU, false);
   double c1 = 0.0;
@@ -638,7 +657,7 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
         c, PC_MISC, 0, 0,
         [&] {
           launch_d2f_pad(T, s.Tf, s.pT->nnzb, s.B, false, c->ws);
-          launch_taylor_init(s.dUf, true, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
+          launch_taylor_init(dUout, true, s.pU->nnzb, s.pU->rowidx, s.pU->col, T, false, s.u_to_t, s.B,
                              terms > 1 ? c1 : 0.0, c1i, 0, c->ws);
         },
         2);
@@ -653,14 +672,14 @@ static void taylor_series(rt_ctx* c, Sys& s, const double* T, double dt, int ter
       // kernels; the generic kernel takes the transpose while staging)
       const bool last = n == terms - 1;
       GemmArgs g = args(s.Tf, prev, last ? nullptr : bufs[n % 2]);
-      g.U = s.dUf;
+      g.U = dUout;
       g.coef = cn;
       g.coef_imag = ci;
-      if (last && s.dUH) g.base = s.dUH;
+      if (last && dUH) g.base = dUH;
       gemm(c, s, PC_TAYLOR, n == 2 ? t2 : tn, true, false, false, false, EPI_STORE_ACC, g, s.pU);
       prev = bufs[n % 2];
     }
-    if (s.dUH && terms < 3) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
+    if (dUH && terms < 3) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(dUout, dUH, s.pU->nnzb, s.B, c->ws); });
   }
 }
 
@@ -682,9 +701,27 @@ static void field_T(rt_ctx* c, Sys& s, int which, double* Tout) {
 }
 
 // ETRS (Sec. II.A): U = cut(exp(-i dt/2 T(t+dt)) exp(-i dt/2 T(t))), each
-// exponential by the truncated Taylor series
-static void build_etrs(rt_ctx* c, Sys& s) {
+// exponential by the truncated Taylor series.  Mixed mode: with the FP32
+// differences dU_a = exp(-i dt/2 T(t)) - I and dU_b = exp(-i dt/2 T(t+dt)) - I
+// (both on P_U, which holds the identity blocks), the cut is linear, so
+//   U - I = dU_a + dU_b + cut(dU_b dU_a)
+// exactly; the fields enter through T(t) = T0 - E(t) T_D.
+static void build_etrs(rt_ctx* c, Sys& s, bool fp32) {
   const rt_params& p = c->p;
+  if (fp32) {
+    const int64_t nT = (int64_t)nvals(s, s.pT);
+    run(c, PC_FIELD, 0, 16.0 * nT, [&] { launch_field_axpy(s.T0, s.TD, c->dstate, E_T, 1.0, s.T, nT, c->ws); });
+    taylor_series(c, s, s.T, 0.5 * p.dt, p.taylor_terms, true, nullptr, s.dUa);
+    run(c, PC_FIELD, 0, 16.0 * nT, [&] { launch_field_axpy(s.T0, s.TD, c->dstate, E_TDT, 1.0, s.T, nT, c->ws); });
+    taylor_series(c, s, s.T, 0.5 * p.dt, p.taylor_terms, true, nullptr, s.dUb);
+    const int64_t nU = (int64_t)nvals32(s, s.pU);
+    run(c, PC_MISC, 0, 0, [&] { launch_axpy32(s.dUf, s.dUa, s.dUb, 1.0f, nU, c->ws); });
+    TripleInfo& tUU = triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);
+    gemm(c, s, PC_TAYLOR, tUU, true, true, false, false, EPI_ADD, args(s.dUb, s.dUa, s.dUf), s.pU);
+    if (s.dUH) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
+    s.duf_current = true;
+    return;
+  }
   field_T(c, s, E_T, s.T);
   taylor_series(c, s, s.T, 0.5 * p.dt, p.taylor_terms, false, s.X);
   field_T(c, s, E_TDT, s.T);
@@ -696,8 +733,50 @@ static void build_etrs(rt_ctx* c, Sys& s) {
 // fourth-order Magnus (Sec. II.A): T1, T2 at t + (1/2 -+ sqrt(3)/6) dt,
 // Om = -i dt/2 (T1 + T2) - sqrt(3) dt^2/12 [T2, T1] on P_U,
 // U = sum_{n<terms} Om^n / n! with Om^n = cut(Om Om^{n-1})
-static void build_m4(rt_ctx* c, Sys& s) {
+static void build_m4(rt_ctx* c, Sys& s, bool fp32) {
   const rt_params& p = c->p;
+  if (fp32) {
+    // mixed mode: T1, T2 = T0 - E(t1,2) T_D; the commutator products and the
+    // powers of Om as FP32 block products; dU = exp(Om) - I accumulated in
+    // FP32 (the identity is never added, as in the other delta forms)
+    const int64_t nT = (int64_t)nvals(s, s.pT);
+    run(
+        c, PC_FIELD, 0, 32.0 * nT,
+        [&] {
+          launch_field_axpy(s.T0, s.TD, c->dstate, E_T1, 1.0, s.T, nT, c->ws);
+          launch_field_axpy(s.T0, s.TD, c->dstate, E_T2, 1.0, s.T2, nT, c->ws);
+        },
+        2);
+    run(
+        c, PC_MISC, 0, 0,
+        [&] {
+          launch_d2f_pad(s.T, s.Tf, s.pT->nnzb, s.B, false, c->ws);
+          launch_d2f_pad(s.T2, s.Tf2, s.pT->nnzb, s.B, false, c->ws);
+        },
+        2);
+    TripleInfo& tTT = triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);
+    gemm(c, s, PC_TAYLOR, tTT, true, false, false, false, EPI_STORE, args(s.Tf2, s.Tf, s.Pf0), s.pU);  // T2 T1
+    gemm(c, s, PC_TAYLOR, tTT, true, false, false, false, EPI_STORE, args(s.Tf, s.Tf2, s.Pf1), s.pU);  // T1 T2
+    run(c, PC_MISC, 0, 0, [&] {
+      launch_m4_omega32(s.T, s.T2, s.u_to_t, s.Pf0, s.Pf1, p.dt, s.Omf, s.dUf, p.taylor_terms > 1, s.pU->nnzb, s.B,
+                        c->ws);
+    });
+    TripleInfo& tUU = triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);
+    const int64_t nU = (int64_t)nvals32(s, s.pU);
+    const float2* prev = s.Omf;
+    float2* bufs[2] = {s.dUa, s.dUb};
+    double inv_fact = 1.0;
+    for (int n = 2; n < p.taylor_terms; ++n) {
+      inv_fact /= n;
+      float2* out = bufs[n % 2];
+      gemm(c, s, PC_TAYLOR, tUU, true, true, false, false, EPI_STORE, args(s.Omf, prev, out), s.pU);
+      run(c, PC_MISC, 0, 0, [&] { launch_axpy32(s.dUf, s.dUf, out, (float)inv_fact, nU, c->ws); });
+      prev = out;
+    }
+    if (s.dUH) run(c, PC_MISC, 0, 0, [&] { launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws); });
+    s.duf_current = true;
+    return;
+  }
   field_T(c, s, E_T1, s.T);
   field_T(c, s, E_T2, s.T2);
   TripleInfo& tTT = triples_for(c, s, s.pT, false, s.pT, false, s.pU, false);
@@ -807,10 +886,10 @@ static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
     }
     return;
   }
-  if (p.prop == RT_PROP_ETRS) {
-    build_etrs(c, s);
-  } else if (p.prop == RT_PROP_M4) {
-    build_m4(c, s);
+  if (p.prop == RT_PROP_ETRS || p.prop == RT_PROP_M4) {
+    if (p.prop == RT_PROP_ETRS) build_etrs(c, s, fp32);
+    else build_m4(c, s, fp32);
+    if (fp32) return;
   } else {
     field_hamiltonian(c, s, E_MID);
     run(c, PC_FIELD, 0, 48.0 * nvals(s, s.pA), [&] {
@@ -1092,7 +1171,7 @@ static void ensure_unitarity_lists(rt_ctx* c, Sys& s) {
 
 static void unitarity(rt_ctx* c, Sys& s, int metric, double* mx, double* mean) {
   ensure_unitarity_lists(c, s);
-  if (c->p.precision == RT_FP32 && c->p.prop == RT_PROP_EM && !c->p.incremental)
+  if (s.duf_current)
     launch_u_from_delta(s.dUf, s.U, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);  // U = I + dU
   if (metric) {
     TripleInfo& tW = triples_for(c, s, s.pS, false, s.pU, false, s.pW, false);
@@ -1314,7 +1393,7 @@ rt_status rt_set_field(rt_ctx* c, const rt_field* f) {
     c->field.sigma = f->sigma;
     c->field.omega = f->omega;
     c->graph_dirty = true;
-    if (dir_changed && c->p.precision == RT_FP32 && c->p.prop == RT_PROP_EM) {
+    if (dir_changed && c->p.precision == RT_FP32 && c->p.prop != RT_PROP_CN) {
       for (auto& sp : c->sys) {
         Sys& s = *sp;
         if (!s.sinv_ready) continue;

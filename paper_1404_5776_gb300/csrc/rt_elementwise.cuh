@@ -52,6 +52,9 @@ void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const 
 void launch_split_u_hilo(const double2* U, float2* hi, float2* lo, int64_t nnzb, const int32_t* rowidx,
                          const int32_t* col, int B, cudaStream_t st);
 void launch_zaxpy(double2* z, const double2* x, const double2* y, double a, int64_t n, cudaStream_t st);
+void launch_axpy32(float2* z, const float2* x, const float2* y, float a, int64_t n, cudaStream_t st);
+void launch_m4_omega32(const double* T1, const double* T2, const int32_t* u_to_t, const float* C21, const float* C12,
+                       double dt, float2* Om, float2* dU, bool first_term, int64_t nnzb_u, int B, cudaStream_t st);
 // V[q] += coef * Q[map[q]] (real Q into the real or, with imag, the imaginary part of V; map null = same
 // blocks, -1 = no block)
 void launch_acc_real(double2* V, const double* Q, const int32_t* map, int64_t nnzb_v, int B, double coef, int imag,

@@ -88,11 +88,48 @@ def test_mixed_field_polynomial(rt, basis):
     assert np.abs(obs[:, 1] - q64).max() <= 1e-6 * np.abs(q64).max()
 
 
-def test_mixed_unitarity_excess(rt):
+@pytest.mark.parametrize("prop", ["etrs", "m4"])
+@pytest.mark.parametrize("basis,radii", [("sp4", dict(r_Sinv=6.0, r_T=6.0, r_U=7.0, r_K=6.0, r_M=7.0)),
+                                         ("spd13", dict(r_Sinv=6.0, r_T=7.0, r_U=6.0, r_K=6.0, r_M=6.0))])
+def test_mixed_etrs_m4_under_pulse(rt, prop, basis, radii):
+    """ETRS and M4 built in FP32 (delta form: U - I from FP32 block products,
+    T(t) = T0 - E(t) T_D) under a Gaussian pulse along z, the field axis set
+    after rt_inverse so that T_D is formed again; U of the last step, the
+    dipole and the charge against the FP64 oracle."""
+    s = synth.diamond_system(2, basis, 6.0, 6.0)
+    K0, _, _ = synth.ground_state_dense(s, 2 * s.n_atoms)
+    steps = 20
+    ctx = rt.RT(s, prop=prop, precision="fp32", **radii)
+    ctx.inverse()
+    ctx.set_field(kind=rt.RT_FIELD_GAUSSIAN, dir=2, E0=5e-3, t0=0.3, sigma=0.2, omega=1.3)
+    ctx.set_density_dense(0, 0, K0)
+    ctx.step(steps)
+    obs = ctx.observables(0, 0)
+    Ug = ctx.matrix(0, rt.RT_MAT_U)
+    Kg = ctx.matrix(0, rt.RT_MAT_K)
+    ctx.close()
+    ref = oracle.Propagator(s, oracle.Params(prop=prop, field={"kind": "gaussian", "E0": 5e-3, "t0": 0.3,
+                                                               "sigma": 0.2, "omega": 1.3}, field_dir=2, **radii))
+    ref.set_density_dense(K0)
+    rows = np.array([[z for z in ref.step()["obs"]] for _ in range(steps)])
+    assert np.abs(Ug - ref.U.val).max() <= 1e-6 * np.abs(ref.U.val).max()
+    p64 = rows[:, 3].real
+    assert np.abs(obs[:, 7] - p64).max() <= 1e-6 * np.abs(p64).max()
+    q64 = rows[:, 0].real
+    assert np.abs(obs[:, 1] - q64).max() <= 1e-6 * np.abs(q64).max()
+    assert np.abs(Kg - ref.K.val).max() <= 1e-5 * np.abs(ref.K.val).max()
+    # the pulse drives the z dipole, and the mixed run follows its induced part
+    ind_g = obs[:, 7] - obs[0, 7]
+    ind_r = p64 - p64[0]
+    assert np.abs(ind_g - ind_r).max() <= 1e-3 * np.abs(ind_r).max()
+
+
+@pytest.mark.parametrize("prop", ["em", "etrs", "m4"])
+def test_mixed_unitarity_excess(rt, prop):
     s = synth.diamond_system(2, "spd13", 6.0, 6.0)
     out = {}
     for prec in ("fp64", "fp32"):
-        ctx = rt.RT(s, precision=prec, **_radii(6.0))
+        ctx = rt.RT(s, prop=prop, precision=prec, **_radii(6.0))
         ctx.inverse()
         ctx.propagator(0.0)
         out[prec] = ctx.unitarity(0, True)
