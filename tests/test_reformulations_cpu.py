@@ -10,6 +10,11 @@ and compared with the literal computation:
 * field polynomial: U(E) = sum_m E^m V_m with V_m = sum_n c_n Q_{n,m},
   Q_{1,0} = T0, Q_{1,1} = -T_D, Q_{n,m} = cut(T0 Q_{n-1,m}) + cut(Q_{1,1} Q_{n-1,m-1}),
   equals the literal truncated series of T(E) at every E.
+* ETRS in the delta form (the mixed path): with dU_a = exp(-i dt/2 T(t)) - I,
+  dU_b = exp(-i dt/2 T(t+dt)) - I and T(t) = T0 - E(t) T_D,
+  I + dU_a + dU_b + cut(dU_b dU_a)  equals  cut(U_b U_a)  from cut(S^-1 H(t)).
+* M4 in the delta form (the mixed path): Om from T1, T2 = T0 - E(t_{1,2}) T_D,
+  I + sum_{n>=1} Om^n / n!  equals the literal M4 propagator from cut(S^-1 H(t_{1,2})).
 The hermitian mirroring of K' (upper blocks computed, lower mirrored) is the
 same on both sides and is applied to both."""
 import math
@@ -136,3 +141,62 @@ def test_field_polynomial_equals_literal_series(setup, terms):
         TE = oracle.spgemm(Sinv, oracle.hamiltonian(H0, D, E), pT)
         U_lit, _ = oracle.taylor_em(TE, dt, terms, pU)
         assert rel(poly, U_lit.val) < 1e-12, (terms, E)
+
+
+PULSE = {"kind": "gaussian", "E0": 0.02, "t0": 0.1, "sigma": 0.2, "omega": 1.1}
+
+
+def _field_split(ref):
+    T0 = oracle.spgemm(ref.Sinv, ref.H0, ref.pats["T"])
+    TD = oracle.spgemm(ref.Sinv, ref.D[ref.p.field_dir], ref.pats["T"])
+    return T0, TD
+
+
+def _T_of(T0, TD, E):
+    return oracle.BlockMatrix(T0.bsize, T0.pat, T0.val - E * TD.val, T0.voff)
+
+
+@pytest.mark.parametrize("r_T,r_U", [(5.0, 7.0), (7.0, 5.0)])
+def test_etrs_delta_form_equals_literal(setup, r_T, r_U):
+    s = setup[0]
+    p = oracle.Params(prop="etrs", r_Sinv=6.0, r_T=r_T, r_U=r_U, r_K=6.0, r_M=6.0, field=PULSE, field_dir=1)
+    ref = oracle.Propagator(s, p)
+    T0, TD = _field_split(ref)
+    pU = ref.pats["U"]
+    I = oracle.identity(s.bsize, pU)
+    for t in (0.0, 0.15):
+        Ua, _ = oracle.taylor_em(_T_of(T0, TD, oracle.field_value(PULSE, t)), 0.5 * p.dt, p.taylor_terms, pU)
+        Ub, _ = oracle.taylor_em(_T_of(T0, TD, oracle.field_value(PULSE, t + p.dt)), 0.5 * p.dt, p.taylor_terms, pU)
+        dUa = oracle.axpy(-1.0, I, Ua)
+        dUb = oracle.axpy(-1.0, I, Ub)
+        delta = oracle.axpy(1.0, oracle.spgemm(dUb, dUa, pU), oracle.axpy(1.0, dUb, oracle.axpy(1.0, dUa, I)))
+        U_lit, _ = ref.propagator(t)
+        assert rel(delta.val, U_lit.val) < 1e-13, t
+        # the correction term is second order in dt: dropping it is visible
+        assert rel(oracle.axpy(1.0, dUb, oracle.axpy(1.0, dUa, I)).val, U_lit.val) > 1e-6
+
+
+@pytest.mark.parametrize("r_T,r_U", [(5.0, 7.0), (7.0, 5.0)])
+def test_m4_delta_form_equals_literal(setup, r_T, r_U):
+    s = setup[0]
+    p = oracle.Params(prop="m4", r_Sinv=6.0, r_T=r_T, r_U=r_U, r_K=6.0, r_M=6.0, field=PULSE, field_dir=2)
+    ref = oracle.Propagator(s, p)
+    T0, TD = _field_split(ref)
+    pU = ref.pats["U"]
+    r3 = math.sqrt(3.0)
+    for t in (0.0, 0.15):
+        T1 = _T_of(T0, TD, oracle.field_value(PULSE, t + (0.5 - r3 / 6.0) * p.dt))
+        T2 = _T_of(T0, TD, oracle.field_value(PULSE, t + (0.5 + r3 / 6.0) * p.dt))
+        C21 = oracle.spgemm(T2, T1, pU)
+        C12 = oracle.spgemm(T1, T2, pU)
+        tsum = oracle.axpy(1.0, oracle.restrict(T2, pU), oracle.restrict(T1, pU))
+        Om = oracle.BlockMatrix(s.bsize, pU, -0.5j * p.dt * tsum.val
+                                - (r3 * p.dt * p.dt / 12.0) * (C21.val - C12.val), tsum.voff)
+        dU = Om.copy()
+        P = Om
+        for n in range(2, p.taylor_terms):
+            P = oracle.spgemm(Om, P, pU)
+            dU = oracle.axpy(1.0 / math.factorial(n), P, dU)
+        U_lit, _ = ref.propagator(t)
+        I = oracle.identity(s.bsize, pU)
+        assert rel(oracle.axpy(1.0, I, dU).val, U_lit.val) < 1e-13, t
