@@ -26,6 +26,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--prop", default="em", choices=["em", "cn", "etrs", "m4"])
     ap.add_argument("--foe-order", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the nvidia-smi clock samples of the timed region (default: a temp dir)")
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed FP64 steps (default: --steps)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the mixed-precision context (FOE ground state, kick, warm-up, steps) and print "
@@ -305,8 +308,8 @@ def run_gpu(args):
         ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
         return ms / max(nsteps, 1)
 
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_r{rank}.csv")
+    clocks_dir = args.clocks_dir or tempfile.gettempdir()
+    clocks = Clocks(os.path.join(clocks_dir, f"clocks_r{rank}.csv"))
     clocks.start()
     ms64 = timed(c64, n64, args.warmup, "fp64")
     ms32 = timed(c32, args.steps, args.warmup, "fp32_mixed")
