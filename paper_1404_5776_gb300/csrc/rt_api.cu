@@ -102,7 +102,7 @@ struct Sys {
   double* rows_tmp = nullptr;
   bool sinv_ready = false;
   bool u_ready = false;
-  bool duf_current = false;  // the FP32 EM mode's U - I holds the last propagator (U itself is not formed)
+  bool duf_current = false;  // U - I in FP32 holds the last propagator (FP32 EM, ETRS, M4: U itself is not formed)
   int sinv_iters = 0;
   double sinv_resid = 0.0;
   std::string sinv_status;
@@ -1810,6 +1810,11 @@ rt_status rt_get_state(rt_ctx* c, void* buf, size_t* bytes) {
     }
     RT_REQUIRE(*bytes >= need, RT_EINVAL, "state buffer too small");
     for (auto& sp : c->sys) materialize(c, *sp);  // the state holds K itself
+    for (auto& sp : c->sys) {
+      // and U itself: where only U - I is current (FP32 EM, ETRS, M4), U = I + (U - I)
+      Sys& s = *sp;
+      if (s.duf_current) launch_u_from_delta(s.dUf, s.U, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
+    }
     char* o = (char*)buf;
     StateHeader h{0x52544b53544154ull, c->host_step, c->t_host, c->n_slots};
     memcpy(o, &h, sizeof(h));
@@ -1878,6 +1883,13 @@ rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
       if (c->p.precision == RT_FP32 && s.dUf) {
         launch_u_minus_i_f32(s.U, s.dUf, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
         if (s.dUH) launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws);
+      }
+      if (s.dUh) {  // incremental form: the FP32 hi + lo parts of the restored U
+        launch_split_u_hilo(s.U, s.dUh, s.dUl, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
+        if (s.dUHh) {
+          launch_dagger32(s.dUh, s.dUHh, s.pU->nnzb, s.B, c->ws);
+          launch_dagger32(s.dUl, s.dUHl, s.pU->nnzb, s.B, c->ws);
+        }
       }
     }
     c->host_step = h.host_step;

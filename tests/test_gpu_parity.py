@@ -298,6 +298,34 @@ def test_checkpoint_resume_bit_exact(rt):
     assert np.array_equal(obs_a[-4:], obs_b[-4:])
 
 
+@pytest.mark.parametrize("prop", ["em", "etrs", "m4"])
+def test_checkpoint_resume_mixed_propagation_step(rt, prop):
+    """Mixed mode with U built once and reused (full_step = 0): only U - I is
+    current (FP32), so the checkpoint carries U = I + (U - I) and the resumed
+    run applies the same propagator (the kick left its own operator in U)."""
+    s = synth.diamond_system(2, "sp4", 6.0, 6.0)
+    K0, _, _ = synth.ground_state_dense(s, s.n // 2)
+    ctx = rt.RT(s, prop=prop, precision="fp32", full_step=0, **_radii(6.0))
+    ctx.inverse()
+    ctx.set_density_dense(0, 0, K0)
+    ctx.kick(0, 0, 0, 1e-3)
+    ctx.propagator(0.0)
+    ctx.step(2)
+    state = ctx.get_state()
+    ctx.step(3)
+    K_a = ctx.matrix(0, rt.RT_MAT_K)
+    obs_a = ctx.observables(0, 0)
+    ctx.set_state(state)
+    ctx.step(3)
+    K_b = ctx.matrix(0, rt.RT_MAT_K)
+    obs_b = ctx.observables(0, 0)
+    ctx.close()
+    assert np.abs(K_b - K_a).max() <= 1e-12 * np.abs(K_a).max()
+    scale = np.abs(obs_a[-3:, 1]).max()  # Tr(KS)
+    for col in (1, 3, 5, 7):  # Tr(KS), Tr(K Dx,y,z)
+        assert np.abs(obs_b[-3:, col] - obs_a[-3:, col]).max() <= 1e-12 * scale, col
+
+
 def test_graph_and_direct_launch_identical(rt):
     s = synth.diamond_system(2, "sp4", 6.0, 6.0)
     K0, _, _ = synth.ground_state_dense(s, s.n // 2)
