@@ -282,8 +282,10 @@ RT_API rt_status rt_profile_read(rt_ctx* ctx, int32_t max, int32_t* n_classes, i
 
 /* Checkpoint: every K, U, the CN warm start, the device step state (time,
  * field samples), the step counter and the observables cursor.  With buf
- * NULL, *bytes receives the size.  rt_set_state restores it (and clears the
- * poisoned state and the device error word). */
+ * NULL, *bytes receives the size.  Where only U - I is current (FP32 EM, ETRS,
+ * M4) the state holds U = I + (U - I).  rt_set_state restores it, forms the
+ * FP32 parts of U that the mixed sandwich uses from it, and clears the
+ * poisoned state and the device error word. */
 RT_API rt_status rt_get_state(rt_ctx* ctx, void* buf, size_t* bytes);
 RT_API rt_status rt_set_state(rt_ctx* ctx, const void* buf, size_t bytes);
 
