@@ -344,6 +344,41 @@ RT_API rt_status rt_synchronize(rt_ctx* ctx);
 enum { RT_FAULT_HOTELLING_MAXITER1 = 1, RT_FAULT_NAN_IN_H = 2, RT_FAULT_WAIT_TIMEOUT_0 = 4 };
 RT_API rt_status rt_debug_inject(rt_ctx* ctx, uint32_t flags);
 
+/* Structural check of one block product's triple list against its patterns
+ * (host arrays; no device work, no context): the contract every block-product
+ * kernel relies on for in-bounds operand loads and race-free stores.  The
+ * truncated product C = cut_{P_C}(op(A) op(B)) (Sec. II.A) is evaluated per
+ * output block (i,j) of P_C as sum over k of op(A)_ik op(B)_kj; a triple list
+ * names, per output item, the operand blocks of each k.
+ *   Patterns: symmetric block-CSR over n_atoms atoms, rowptr[n_atoms+1] from
+ *   0 and non-decreasing, col[] in range and strictly ascending in a row.
+ *   Items: item_blk[n_items] lists the blocks of P_C (with upper_only, the
+ *   blocks with col >= row) in increasing order, one item each, so every
+ *   output block has exactly one writer and an upper-only product never has
+ *   a mirrored (lower) block as an item.
+ *   ptr[n_items+1]: ptr[0] = 0, non-decreasing, ptr[n_items] = n_triples.
+ *   ab[n_triples][2]: for the item's block (i,j), a indexes the stored block
+ *   (i,k) of A ((k,i) when a_dag), b the stored block (k,j) of B ((j,k) when
+ *   b_dag), both within their pattern; k strictly ascending within an item;
+ *   complete: one triple for every k with (i,k) in P_A and (k,j) in P_B.
+ * Returns RT_OK, RT_EINTERNAL if a condition fails (*bad_item, if not NULL,
+ * receives the first failing item, or -1 when the failure is not tied to an
+ * item), or RT_EINVAL for NULL arrays or negative counts. */
+RT_API rt_status rt_check_triples(int32_t n_atoms, const int32_t* a_rowptr, const int32_t* a_col, int32_t a_dag,
+                                  const int32_t* b_rowptr, const int32_t* b_col, int32_t b_dag,
+                                  const int32_t* c_rowptr, const int32_t* c_col, int32_t upper_only,
+                                  int64_t n_items, const int32_t* item_blk, const int64_t* ptr, const int32_t* ab,
+                                  int64_t n_triples, int64_t* bad_item);
+
+/* Debug check of a live context: copies every pattern and every triple list
+ * that the context has built (all systems) back to the host and applies the
+ * checks of rt_check_triples to each.  Synchronises the context stream.
+ * *n_checked (may be NULL) receives the number of triple lists checked.  A
+ * failing list returns RT_EINTERNAL (the product is named in rt_last_error)
+ * and, like every internal error, leaves the context refused until
+ * rt_set_state. */
+RT_API rt_status rt_debug_check(rt_ctx* ctx, int64_t* n_checked);
+
 /* Reason of the last failure (never NULL; "" after success). */
 RT_API const char* rt_last_error(rt_ctx* ctx);
 

@@ -39,7 +39,7 @@ EXPORTED = ["rt_default_params", "rt_create", "rt_set_field", "rt_inverse", "rt_
             "rt_kick", "rt_propagator", "rt_step", "rt_observables", "rt_pattern_size", "rt_get_pattern",
             "rt_matrix_size", "rt_get_matrix", "rt_unitarity", "rt_step_work", "rt_step_kernels", "rt_profile", "rt_profile_read",
             "rt_get_state", "rt_set_state", "rt_synchronize", "rt_last_error", "rt_destroy", "rt_traces_noalloc",
-            "rt_debug_inject"]
+            "rt_debug_inject", "rt_check_triples", "rt_debug_check"]
 
 
 class rt_system(ctypes.Structure):
@@ -110,6 +110,8 @@ def load(path: Optional[str] = None):
         "rt_set_state": [P, P, ctypes.c_size_t],
         "rt_synchronize": [P],
         "rt_debug_inject": [P, ctypes.c_uint32],
+        "rt_check_triples": [I32, P, P, I32, P, P, I32, P, P, I32, I64, P, P, P, I64, P],
+        "rt_debug_check": [P, P],
         "rt_traces_noalloc": [P, I64, P, P, P, I32, P, P, P, P, P, P, I32, P, P],
     }
     for name, args in sig.items():
@@ -142,6 +144,23 @@ def rt_default_params() -> rt_params:
     p = rt_params()
     _check(None, load().rt_default_params(ctypes.byref(p)))
     return p
+
+
+def rt_check_triples(n_atoms, a_rowptr, a_col, a_dag, b_rowptr, b_col, b_dag, c_rowptr, c_col, upper_only,
+                     item_blk, ptr, ab):
+    """Structural check of a triple list against its patterns (host arrays,
+    no GPU; the conditions are those of rt_check_triples in rt.h).  ab is an
+    (n_triples, 2) array of (A block, B block).  Returns (status, bad_item)."""
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    a_rowptr, a_col, b_rowptr, b_col, c_rowptr, c_col, item_blk = map(
+        i32, (a_rowptr, a_col, b_rowptr, b_col, c_rowptr, c_col, item_blk))
+    ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+    ab = np.ascontiguousarray(ab, dtype=np.int32).reshape(-1, 2)
+    bad = ctypes.c_int64(-1)
+    st = load().rt_check_triples(int(n_atoms), _p(a_rowptr), _p(a_col), int(a_dag), _p(b_rowptr), _p(b_col),
+                                 int(b_dag), _p(c_rowptr), _p(c_col), int(upper_only), int(item_blk.size),
+                                 _p(item_blk), _p(ptr), _p(ab), int(ab.shape[0]), ctypes.byref(bad))
+    return st, bad.value
 
 
 def _check(ctx, st):
@@ -373,6 +392,13 @@ class RT:
     def debug_inject(self, flags: int):
         """Host-side fault injection (RT_FAULT_* flags) for tests."""
         self._c(self.lib.rt_debug_inject(self.ctx, flags))
+
+    def debug_check(self) -> int:
+        """Structural check of every pattern and triple list the context has
+        built (rt_debug_check); returns the number of lists checked."""
+        n = ctypes.c_int64(0)
+        self._c(self.lib.rt_debug_check(self.ctx, ctypes.byref(n)))
+        return n.value
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

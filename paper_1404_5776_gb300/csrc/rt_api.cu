@@ -284,6 +284,10 @@ static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cpl
   g.zero = c->zero32;
   g.err = c->d_err;
   g.wait_ns = c->wait_ns;
+  // each output block is written by the one item that owns it while every
+  // item reads the operands: an output or accumulator aliasing an operand races
+  RT_REQUIRE(!g.C || (g.C != g.A && g.C != g.B), RT_EINTERNAL, "block product output aliases an operand");
+  RT_REQUIRE(!g.U || (g.U != g.A && g.U != g.B), RT_EINTERNAL, "block product accumulator aliases an operand");
   int B = s.B;
   run(c, cls, gemm_flops(ti, cplx), gemm_bytes(s, ti, cplx, fp32),
       [&] { launch_gemm(B, fp32, cplx, ad, bd, epi, g, c->ws); });
@@ -1897,6 +1901,45 @@ rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
     RT_CUDA_CHECK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->ws));  // the restored state is sound again
     c->graph_dirty = true;
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    return RT_OK;
+  });
+}
+
+rt_status rt_debug_check(rt_ctx* c, int64_t* n_checked) {
+  return guarded(c, [&] {
+    int64_t n = 0;
+    for (size_t si = 0; si < c->sys.size(); ++si) {
+      Sys& s = *c->sys[si];
+      for (auto& kv : s.tcache) {
+        const TripleKey& key = kv.first;
+        const Triples& T = kv.second->t;
+        std::vector<int32_t> items((size_t)T.n_items);
+        std::vector<int64_t> ptr((size_t)T.n_items + 1, 0);
+        std::vector<int32_t> ab((size_t)(2 * T.n_triples));
+        if (T.n_items) {
+          RT_CUDA_CHECK(cudaMemcpyAsync(items.data(), T.item_blk, sizeof(int32_t) * items.size(),
+                                        cudaMemcpyDeviceToHost, c->ws));
+          RT_CUDA_CHECK(cudaMemcpyAsync(ptr.data(), T.ptr, sizeof(int64_t) * ptr.size(), cudaMemcpyDeviceToHost, c->ws));
+        }
+        if (T.n_triples)
+          RT_CUDA_CHECK(cudaMemcpyAsync(ab.data(), T.ab, sizeof(int2) * (size_t)T.n_triples, cudaMemcpyDeviceToHost,
+                                        c->ws));
+        RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+        int64_t bad = -1;
+        std::string why;
+        const bool ok = check_triples_host(
+            s.n_atoms, key.A->h_rowptr.data(), key.A->h_col.data(), key.ad, key.B->h_rowptr.data(),
+            key.B->h_col.data(), key.bd, key.C->h_rowptr.data(), key.C->h_col.data(), key.up, T.n_items, items.data(),
+            ptr.data(), ab.data(), T.n_triples, &bad, &why);
+        RT_REQUIRE(ok, RT_EINTERNAL,
+                   "triple list of system " + std::to_string(si) + " (P_A r = " + std::to_string(key.A->radius) +
+                       (key.ad ? " dagger" : "") + ", P_B r = " + std::to_string(key.B->radius) +
+                       (key.bd ? " dagger" : "") + ", P_C r = " + std::to_string(key.C->radius) +
+                       (key.up ? " upper" : "") + ") fails at item " + std::to_string(bad) + ": " + why);
+        ++n;
+      }
+    }
+    if (n_checked) *n_checked = n;
     return RT_OK;
   });
 }

@@ -110,6 +110,13 @@ void build_transpose_map(int32_t* map, const Pattern& src, const Pattern& dst, c
 // exclusive scan of int64 counts (n+1 outputs, out[n] = total); returns total
 int64_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Arena& arena, cudaStream_t st);
 
+// Structural check of a triple list against its patterns (host arrays; the
+// conditions of rt_check_triples).  False with the reason in *why on failure.
+bool check_triples_host(int n, const int32_t* a_rp, const int32_t* a_col, bool a_dag, const int32_t* b_rp,
+                        const int32_t* b_col, bool b_dag, const int32_t* c_rp, const int32_t* c_col, bool upper_only,
+                        int64_t n_items, const int32_t* item_blk, const int64_t* ptr, const int32_t* ab,
+                        int64_t n_triples, int64_t* bad_item, std::string* why);
+
 // ----------------------------------------------------------------------------
 // block products
 // ----------------------------------------------------------------------------
