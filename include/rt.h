@@ -150,11 +150,26 @@ typedef struct {
   int32_t kick_terms;       /* Taylor terms of the kick exponential               */
   int32_t obs_capacity;     /* steps kept in the observables buffer               */
   int32_t use_graph;        /* capture the step in a CUDA graph and replay it     */
-  int32_t incremental;      /* with RT_FP32 and full_step = 0 (constant U, built in
-                               FP64): propagate dK = K - K_ref, K_ref = K at the
-                               first step after K or U changed, with
-                               R = U K_ref U^dagger - K_ref in FP64 and U - I as
-                               FP32 hi + lo; 13-function systems only          */
+  int32_t incremental;      /* reference split (RT_FP32, systems of block size 4 or 13):
+                               K = K_ref + dK, K_ref = K at the first step after
+                               K changed (or, with full_step = 0, U changed).  The
+                               part of the step acting on K_ref,
+                               R = sym(cut(cut(U K_ref) U^dagger)) - K_ref, is
+                               FP64: once for a constant U (full_step = 0, U
+                               built in FP64 by rt_propagator, any propagator),
+                               or, with full_step = 1 and the EM field
+                               polynomial (field_poly = 1), per step as
+                               R(E) = sum_p E^p B_p at E = E(t + dt/2), the
+                               B_p = sum_{m+m'=p} sym(cut(cut(V_m K_ref) V_m'^dagger))
+                               formed in FP64 when the reference is set (every
+                               cut is linear; exact for H = H0 - E D).  The FP32
+                               block products act on the small dK only, with
+                               U - I stochastically rounded to FP32 afresh at
+                               every step (counter-based draws keyed on the step
+                               and element; an unbiased rounding, so its error
+                               does not accumulate as a drift).  Memory with
+                               full_step = 1: (2 taylor_terms - 1) complex FP64
+                               matrices on P_K per kick, taylor_terms on P_M    */
   int32_t field_poly;       /* EM only: build U(t) each step as the polynomial
                                U = sum_m E^m V_m in the field value E = E(t+dt/2).
                                H = H0 - E D and every cut being linear, the
@@ -229,8 +244,8 @@ RT_API rt_status rt_kick(rt_ctx* ctx, int32_t sys, int32_t kick, int32_t dir, do
 
 /* Builds U for [t, t+dt] for every system with the context's propagator
  * (EM at the midpoint, its field polynomial, ETRS, M4 or the CN form) and
- * keeps it for steps with full_step = 0 (in the incremental form also as FP32
- * hi + lo parts).  Synchronises. */
+ * keeps it for steps with full_step = 0 (in the reference split in FP64).
+ * Synchronises. */
 RT_API rt_status rt_propagator(rt_ctx* ctx, double t);
 
 /* n time steps K <- U K U^dagger for every (system, kick), each followed by the
@@ -315,7 +330,8 @@ RT_API rt_status rt_set_state(rt_ctx* ctx, const void* buf, size_t bytes);
  * looks up the array's device address (cudaGetSymbolAddress) and should come
  * before any stream capture.  Work is enqueued on cuda_stream (NULL = legacy
  * default stream); the call does not synchronise.  Errors: RT_EINVAL, RT_ECUDA
- * (reason printed on stderr). */
+ * (reason printed on stderr); a CUDA error already pending from the caller's
+ * earlier work is reported as RT_ECUDA and left pending, not consumed. */
 #define RT_NOALLOC_MAX_CTAS 1024
 RT_API rt_status rt_traces_noalloc(const double* K, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
                                    const int32_t* bsize, int32_t B, const double* S, const int32_t* ks_map,

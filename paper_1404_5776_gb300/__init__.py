@@ -32,6 +32,7 @@ RT_FIELD_NONE, RT_FIELD_GAUSSIAN, RT_FIELD_CONSTANT = 0, 1, 2
 RT_MAT_S, RT_MAT_H0, RT_MAT_DX, RT_MAT_DY, RT_MAT_DZ, RT_MAT_SINV, RT_MAT_T, RT_MAT_U, RT_MAT_K, RT_MAT_X = range(10)
 RT_PAT_S, RT_PAT_H, RT_PAT_SINV, RT_PAT_T, RT_PAT_U, RT_PAT_K, RT_PAT_M, RT_PAT_A, RT_PAT_W = range(9)
 RT_NOBS = 12
+RT_NOALLOC_MAX_CTAS = 1024
 OBS_FIELDS = ["t", "trks_re", "trks_im", "trkdx_re", "trkdx_im", "trkdy_re", "trkdy_im", "trkdz_re", "trkdz_im",
               "herm", "hot_iters", "hot_resid"]
 

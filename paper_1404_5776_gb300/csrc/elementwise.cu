@@ -687,33 +687,96 @@ void launch_u_from_delta(const float2* dU, double2* U, int64_t nnzb, const int32
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
-// Incremental form: U - I split into FP32 hi + lo parts (FP32 block layout),
-// so that hi + lo carries U - I to about 2^-48 relative.
-__global__ void k_split_u_hilo(const double2* __restrict__ U, float2* __restrict__ hi, float2* __restrict__ lo,
-                               int64_t nnzb, const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B,
-                               int rs) {
+// Stochastic rounding to FP32 (reference-split form).  A fixed FP32 rounding
+// of U - I is the same perturbation of the propagator at every step, and its
+// effect on the induced dipole grows linearly with the step count; rounding
+// each element to one of its two neighbouring floats at random, with the
+// probabilities that make the result unbiased, turns that drift into a random
+// walk.  The uniform draws come from a counter: the SplitMix64 output function
+// (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014) of a key made of the step number and the element index, so a
+// run is reproducible and a replayed step graph draws fresh numbers.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// x rounded to the float f nearest x or to its neighbour g on the other side
+// of x, g with probability (x - f) / (g - f): E[result] = x.
+__device__ __forceinline__ float round_sr(double x, uint64_t key) {
+  const float f = __double2float_rn(x);
+  const double fd = (double)f;
+  if (fd == x || !isfinite(f)) return f;
+  const float g = nextafterf(f, x > fd ? INFINITY : -INFINITY);
+  const double p = (x - fd) / ((double)g - fd);  // in (0, 1/2]
+  const double u = (double)(splitmix64(key) >> 11) * 0x1.0p-53;
+  return u < p ? g : f;
+}
+
+__device__ __forceinline__ uint64_t sr_key(int64_t step, int64_t idx, int part) {
+  return ((uint64_t)step << 32) ^ (uint64_t)(2 * idx + part);
+}
+
+// dU = U - I stochastically rounded to FP32 (FP32 block layout) and its
+// per-block conjugate transpose dUH, from a constant FP64 U; the draws are
+// keyed on the step number held in the device state.
+__global__ void k_round_u_sr(const double2* __restrict__ U, float2* __restrict__ dU, float2* __restrict__ dUH,
+                             int64_t nnzb, const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B,
+                             int rs, const DevState* __restrict__ s) {
+  const int64_t step = s->step;
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t NE = (int64_t)B * B;
+  const int64_t NE = (int64_t)B * B;
   for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t q = idx / NE;
-    int e = (int)(idx - q * NE);
-    int r = e / B, c = e - r * B;
-    double2 u = U[idx];
-    double dr = u.x - ((rowidx[q] == col[q] && r == c) ? 1.0 : 0.0), di = u.y;
-    float hr = (float)dr, hi_ = (float)di;
-    int64_t o = q * (int64_t)B * rs + r * rs + c;
-    hi[o] = make_float2(hr, hi_);
-    lo[o] = make_float2((float)(dr - (double)hr), (float)(di - (double)hi_));
+    const int64_t q = idx / NE;
+    const int e = (int)(idx - q * NE);
+    const int r = e / B, c = e - r * B;
+    const double2 u = U[idx];
+    const double d = (rowidx[q] == col[q] && r == c) ? 1.0 : 0.0;
+    const float2 f = make_float2(round_sr(u.x - d, sr_key(step, idx, 0)), round_sr(u.y, sr_key(step, idx, 1)));
+    dU[q * (int64_t)B * rs + r * rs + c] = f;
+    if (dUH) dUH[q * (int64_t)B * rs + c * rs + r] = make_float2(f.x, -f.y);
   }
 }
 
-void launch_split_u_hilo(const double2* U, float2* hi, float2* lo, int64_t nnzb, const int32_t* rowidx,
-                         const int32_t* col, int B, cudaStream_t st) {
+void launch_round_u_sr(const double2* U, float2* dU, float2* dUH, int64_t nnzb, const int32_t* rowidx,
+                       const int32_t* col, int B, const DevState* s, cudaStream_t st) {
   int64_t n = nnzb * B * B;
   if (n == 0) return;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  k_split_u_hilo<<<(unsigned)g, 256, 0, st>>>(U, hi, lo, nnzb, rowidx, col, B, rs32(B));
+  k_round_u_sr<<<(unsigned)g, 256, 0, st>>>(U, dU, dUH, nnzb, rowidx, col, B, rs32(B), s);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+// R = sum_{p<=deg} E^p C_p (Horner, FP64) on the upper blocks (col >= row) of
+// a pattern, E = s->E[which]; the lower blocks of R are not written.
+__global__ void k_poly_upper(PolyTerms C, int deg, const DevState* __restrict__ s, int which, double2* __restrict__ R,
+                             int64_t nnzb, const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col,
+                             int64_t NE) {
+  const double E = s->E[which];
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = idx / NE;
+    if (col[q] < rowidx[q]) continue;
+    double2 v = C.v[deg][idx];
+    for (int p = deg - 1; p >= 0; --p) {
+      const double2 cp = C.v[p][idx];
+      v = make_double2(v.x * E + cp.x, v.y * E + cp.y);
+    }
+    R[idx] = v;
+  }
+}
+
+void launch_poly_upper(const PolyTerms& C, int deg, const DevState* s, int which, double2* R, int64_t nnzb,
+                       const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st) {
+  RT_REQUIRE(deg >= 0 && deg < RT_MAX_POLY, RT_EINTERNAL, "polynomial degree out of range");
+  int64_t n = nnzb * B * B;
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_poly_upper<<<(unsigned)g, 256, 0, st>>>(C, deg, s, which, R, nnzb, rowidx, col, (int64_t)B * B);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -820,8 +883,10 @@ void launch_acc_real(double2* V, const double* Q, const int32_t* map, int64_t nn
 
 __global__ void k_field_poly(PolyTerms V, int deg, const DevState* __restrict__ s, int which, double2* __restrict__ U,
                              float2* __restrict__ dU, float2* __restrict__ dUH, int64_t nnzb,
-                             const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B, int rs) {
+                             const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B, int rs,
+                             int stochastic) {
   const double E = s->E[which];
+  const int64_t step = s->step;
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t NE = (int64_t)B * B;
   for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -836,7 +901,8 @@ __global__ void k_field_poly(PolyTerms V, int deg, const DevState* __restrict__ 
       const int e = (int)(idx - q * NE);
       const int r = e / B, c = e - r * B;
       const double d = (rowidx[q] == col[q] && r == c) ? 1.0 : 0.0;
-      const float2 f = make_float2((float)(u.x - d), (float)u.y);
+      const float2 f = stochastic ? make_float2(round_sr(u.x - d, sr_key(step, idx, 0)), round_sr(u.y, sr_key(step, idx, 1)))
+                                  : make_float2((float)(u.x - d), (float)u.y);
       dU[q * (int64_t)B * rs + r * rs + c] = f;
       if (dUH) dUH[q * (int64_t)B * rs + c * rs + r] = make_float2(f.x, -f.y);
     }
@@ -844,13 +910,15 @@ __global__ void k_field_poly(PolyTerms V, int deg, const DevState* __restrict__ 
 }
 
 void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which, double2* U, float2* dU,
-                       float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st) {
+                       float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st,
+                       bool stochastic) {
   RT_REQUIRE(deg >= 0 && deg < RT_MAX_POLY, RT_EINTERNAL, "field polynomial degree out of range");
   int64_t n = nnzb * B * B;
   if (n == 0) return;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
-  k_field_poly<<<(unsigned)g, 256, 0, st>>>(V, deg, s, which, U, dU, dUH, nnzb, rowidx, col, B, rs32(B));
+  k_field_poly<<<(unsigned)g, 256, 0, st>>>(V, deg, s, which, U, dU, dUH, nnzb, rowidx, col, B, rs32(B),
+                                            stochastic ? 1 : 0);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -61,7 +61,7 @@ double* g_scratch_addr[kMaxDevices] = {nullptr};
 rt_status scratch_for_current_device(double** out, const char** why) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
+    cudaGetLastError();  // the error of this lookup itself (nothing was pending before it)
     *why = "no usable current CUDA device";
     return RT_ECUDA;
   }
@@ -70,7 +70,7 @@ rt_status scratch_for_current_device(double** out, const char** why) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_trace_scratch);
     if (e != cudaSuccess || !p) {
-      cudaGetLastError();
+      cudaGetLastError();  // the error of this lookup itself (nothing was pending before it)
       *why = "cudaGetSymbolAddress of the scratch array failed";
       return RT_ECUDA;
     }
@@ -107,6 +107,13 @@ RT_API rt_status rt_traces_noalloc(const double* K, int64_t nnzb, const int32_t*
   if (nb < 1 || nb > kMaxCtas)
     return fail(RT_EINVAL, "n_ctas = " + std::to_string(n_ctas) + " is outside 1.." + std::to_string(kMaxCtas) +
                                " (the scratch holds RT_NOALLOC_MAX_CTAS partial sums)");
+  // An error left pending by the caller's earlier work is reported as such and
+  // left in place (not consumed): only errors of this call's own launches are
+  // read and cleared below.
+  cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess)
+    return fail(RT_ECUDA, std::string("a CUDA error from earlier work is pending (not cleared): ") +
+                              cudaGetErrorString(pending));
   double* scratch = nullptr;
   const char* why = nullptr;
   rt_status st = scratch_for_current_device(&scratch, &why);
@@ -115,7 +122,7 @@ RT_API rt_status rt_traces_noalloc(const double* K, int64_t nnzb, const int32_t*
   k_traces<<<nb, kThreads, 0, s>>>(reinterpret_cast<const double2*>(K), nnzb, rowidx, col, bsize, B, S, ks_map, Dx,
                                    Dy, Dz, kd_map, scratch);
   k_traces_final_out<<<1, kThreads, 0, s>>>(scratch, nb, out);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();  // nothing was pending before the launches: this error is theirs
   if (e != cudaSuccess) return fail(RT_ECUDA, std::string("launch failed: ") + cudaGetErrorString(e));
   return RT_OK;
 }

@@ -86,11 +86,19 @@ struct Sys {
   float* Tf2 = nullptr;
   // FP32 Hotelling iterations of the mixed CN step: A on P_A, X, Y = A X (then 2I - A X), X Y on P_U
   float2 *Acn32 = nullptr, *X32 = nullptr, *Y32 = nullptr, *Xn32 = nullptr;
-  // incremental form (FP32, constant U): K = K_ref + dK, R = U K_ref U^dagger - K_ref
-  std::vector<double2*> Kref, dK, Rm;
-  std::vector<double*> tref;      // reference traces (8 doubles per kick)
-  std::vector<char> ref_fresh;    // dK holds K - K_ref for this kick (K itself is stale)
-  float2 *dUh = nullptr, *dUl = nullptr, *dUHh = nullptr, *dUHl = nullptr, *Nf = nullptr, *Mlo = nullptr;
+  // reference split (FP32): K = K_ref + dK[kick] with one K_ref per system (the kicks of a
+  // system stay O(kappa) apart), R = sym(cut(cut(U K_ref) U^dagger)) - K_ref in FP64
+  // (constant U: R formed once; field polynomial: R(E) = sum_p E^p Bp[p] formed per step)
+  double2 *Kref = nullptr, *Rm = nullptr;
+  double* tref = nullptr;         // traces of K_ref (8 doubles)
+  std::vector<double2*> dK;       // per kick
+  std::vector<char> dk_fresh;     // per kick: dK holds K - K_ref (K itself is stale)
+  bool ref_ready = false;         // K_ref and its traces are formed
+  bool r_ready = false;           // R (constant U) or the Bp (field polynomial) match K_ref and U
+  std::vector<double2*> Am;       // cut(V_m K_ref) on P_M while Bp is formed
+  std::vector<double2*> Bp;       // coefficients of R(E) on P_K (Bp[0] includes -K_ref)
+  float2 *dUr = nullptr, *dUHr = nullptr;  // U - I stochastically rounded to FP32, and its block dagger
+  bool u64_stale = false;         // the FP64 U is not formed per step (field polynomial, reference split)
   // maps
   int32_t *u_to_t = nullptr, *a_to_s = nullptr, *a_to_h = nullptr, *k_to_sT = nullptr, *k_to_hT = nullptr;
   int32_t *u_to_sinv = nullptr, *k_to_sinv = nullptr, *u_to_s = nullptr, *k_to_m = nullptr, *m_to_k = nullptr;
@@ -149,6 +157,7 @@ struct rt_ctx {
   std::vector<PendingEv> pending;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
   bool poisoned = false;
+  bool unrecoverable = false;  // a drain of copies in flight gave up: shared memory may have been written late
   std::string err;
 };
 
@@ -285,9 +294,25 @@ static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cpl
   g.err = c->d_err;
   g.wait_ns = c->wait_ns;
   // each output block is written by the one item that owns it while every
-  // item reads the operands: an output or accumulator aliasing an operand races
-  RT_REQUIRE(!g.C || (g.C != g.A && g.C != g.B), RT_EINTERNAL, "block product output aliases an operand");
-  RT_REQUIRE(!g.U || (g.U != g.A && g.U != g.B), RT_EINTERNAL, "block product accumulator aliases an operand");
+  // item reads the operands: an output or accumulator overlapping an operand
+  // (the same buffer or any part of it) races
+  {
+    const size_t vbytes = (cplx ? 2 : 1) * (fp32 ? 4 : 8);
+    const size_t op_blk = (size_t)(fp32 ? sb32(s.B) : s.B * s.B) * vbytes;
+    const size_t out_blk = epi == EPI_DELTA_SANDWICH ? (size_t)s.B * s.B * 16 : op_blk;
+    const size_t acc_blk = (size_t)(fp32 ? sb32(s.B) * 8 : s.B * s.B * 16);
+    auto overlaps = [](const void* p, size_t np, const void* q, size_t nq) {
+      const char *a = (const char*)p, *b = (const char*)q;
+      return p && q && a < b + nq && b < a + np;
+    };
+    const size_t nA = (size_t)ti.nnzb_a * op_blk, nB = (size_t)ti.nnzb_b * op_blk;
+    const size_t nC = C ? (size_t)C->nnzb * out_blk : 1;
+    const size_t nU = (C && !g.umap) ? (size_t)C->nnzb * acc_blk : 1;
+    RT_REQUIRE(!overlaps(g.C, nC, g.A, nA) && !overlaps(g.C, nC, g.B, nB), RT_EINTERNAL,
+               "block product output overlaps an operand");
+    RT_REQUIRE(!overlaps(g.U, nU, g.A, nA) && !overlaps(g.U, nU, g.B, nB), RT_EINTERNAL,
+               "block product accumulator overlaps an operand");
+  }
   int B = s.B;
   run(c, cls, gemm_flops(ti, cplx), gemm_bytes(s, ti, cplx, fp32),
       [&] { launch_gemm(B, fp32, cplx, ad, bd, epi, g, c->ws); });
@@ -516,28 +541,18 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
     for (int m = 0; m < p.taylor_terms; ++m) s.V.push_back(c->arena.get_n<double2>(nvals(s, s.pU)));
   }
   if (p.incremental) {
-    // incremental form for a constant propagator (13-function blocks)
-    RT_REQUIRE(s.B == 13, RT_EINVAL, "the incremental form needs 13-function atoms (block size 13)");
-    for (int k = 0; k < p.n_kick; ++k) {
-      s.Kref.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
-      s.dK.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
-      s.Rm.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
-      s.tref.push_back(c->arena.get_n<double>(8));
-    }
-    s.ref_fresh.assign(p.n_kick, 0);
-    s.dUh = c->arena.get_n<float2>(nvals32(s, s.pU));
-    s.dUl = c->arena.get_n<float2>(nvals32(s, s.pU));
-    s.Nf = c->arena.get_n<float2>(nvals32(s, s.pK));
-    s.Mlo = c->arena.get_n<float2>(nvals32(s, s.pM));
-    RT_CUDA_CHECK(cudaMemsetAsync(s.Mlo, 0, sizeof(float2) * nvals32(s, s.pM), c->ws));
-    RT_CUDA_CHECK(cudaMemsetAsync(s.dUh, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
-    RT_CUDA_CHECK(cudaMemsetAsync(s.dUl, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
-    RT_CUDA_CHECK(cudaMemsetAsync(s.Nf, 0, sizeof(float2) * nvals32(s, s.pK), c->ws));
-    if (s.B == 13) {
-      s.dUHh = c->arena.get_n<float2>(nvals32(s, s.pU));
-      s.dUHl = c->arena.get_n<float2>(nvals32(s, s.pU));
-      RT_CUDA_CHECK(cudaMemsetAsync(s.dUHh, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
-      RT_CUDA_CHECK(cudaMemsetAsync(s.dUHl, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+    // reference split K = K_ref + dK (block sizes 4 and 13: the FP32 kernels that take R)
+    RT_REQUIRE(s.B == 13 || s.B == 4, RT_EINVAL, "the reference split needs block size 4 or 13");
+    s.Kref = c->arena.get_n<double2>(nvals(s, s.pK));
+    s.Rm = c->arena.get_n<double2>(nvals(s, s.pK));
+    s.tref = c->arena.get_n<double>(8);
+    for (int k = 0; k < p.n_kick; ++k) s.dK.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
+    s.dk_fresh.assign(p.n_kick, 0);
+    s.dUr = c->arena.get_n<float2>(nvals32(s, s.pU));
+    RT_CUDA_CHECK(cudaMemsetAsync(s.dUr, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+    if (s.B == 13) {  // the 13-function kernels read a pre-transposed dagger
+      s.dUHr = c->arena.get_n<float2>(nvals32(s, s.pU));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.dUHr, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
     }
   }
   RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
@@ -816,6 +831,7 @@ static void build_m4(rt_ctx* c, Sys& s, bool fp32) {
 // U(E) = I + sum_n c_n T^n(E) = sum_m E^m V_m, V_m = sum_n c_n Q_{n,m} (+ I in V_0).
 static void build_field_poly(rt_ctx* c, Sys& s) {
   const rt_params& p = c->p;
+  s.r_ready = false;  // the reference split's B_p follow the V_m
   const int deg = p.taylor_terms - 1;
   Pattern* PT = s.pT;
   Pattern* PU = s.pU;
@@ -1003,68 +1019,145 @@ static void observe(rt_ctx* c, Sys& s, int kick, int slot) {
       [&] {
         launch_traces(incr ? s.dK[kick] : s.K[kick], s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S,
                       s.k_to_sT, s.D[0], s.D[1], s.D[2], s.k_to_hT, s.red_part, c->dstate, slot, c->ring,
-                      c->p.obs_capacity, c->n_slots, slot, c->ws, incr ? s.tref[kick] : nullptr, nullptr);
+                      c->p.obs_capacity, c->n_slots, slot, c->ws, incr ? s.tref : nullptr, nullptr);
       },
       2);
 }
 
-// K = K_ref + dK for kicks whose K is stale (before K is read or replaced)
-static void materialize(rt_ctx* c, Sys& s) {
-  for (size_t k = 0; k < s.ref_fresh.size(); ++k) {
-    if (!s.ref_fresh[k]) continue;
-    launch_zaxpy(s.K[k], s.Kref[k], s.dK[k], 1.0, (int64_t)nvals(s, s.pK), c->ws);
-    s.ref_fresh[k] = 0;
+// K = K_ref + dK for the kicks whose K is stale.  keep = false hands K back
+// as the authoritative density (the next step forms dK = K - K_ref again);
+// a read (keep = true) leaves dK in place, so the run continues unchanged.
+static void materialize(rt_ctx* c, Sys& s, bool keep = false) {
+  for (size_t k = 0; k < s.dk_fresh.size(); ++k) {
+    if (!s.dk_fresh[k]) continue;
+    launch_zaxpy(s.K[k], s.Kref, s.dK[k], 1.0, (int64_t)nvals(s, s.pK), c->ws);
+    if (!keep) s.dk_fresh[k] = 0;
   }
 }
 
-// K_ref = K, dK = 0, R = cut(cut(U K_ref) U^dagger) - K_ref (FP64 sandwich),
-// reference traces Tr(K_ref X)
-static void make_reference(rt_ctx* c, Sys& s, int kick) {
-  const size_t nv = nvals(s, s.pK);
-  RT_CUDA_CHECK(cudaMemcpyAsync(s.Kref[kick], s.K[kick], sizeof(double2) * nv, cudaMemcpyDeviceToDevice, c->ws));
-  RT_CUDA_CHECK(cudaMemsetAsync(s.dK[kick], 0, sizeof(double2) * nv, c->ws));
-  TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
-  TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
-  gemm(c, s, PC_MISC, tM, false, true, false, false, EPI_STORE, args(s.U, s.Kref[kick], s.M), s.pM);
-  gemm(c, s, PC_MISC, tK, false, true, false, true, EPI_SANDWICH, args(s.M, s.U, s.Rm[kick]), s.pK);
-  launch_zaxpy(s.Rm[kick], s.Rm[kick], s.Kref[kick], -1.0, (int64_t)nv, c->ws);
-  launch_traces(s.Kref[kick], s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S, s.k_to_sT, s.D[0], s.D[1],
-                s.D[2], s.k_to_hT, s.red_part, c->dstate, 0, c->ring, c->p.obs_capacity, c->n_slots, 0, c->ws, nullptr,
-                s.tref[kick]);
-  s.ref_fresh[kick] = 1;
+// FP64 U of the last step where only its FP32 rounding was formed (field
+// polynomial in the reference split): U = sum_m E^m V_m at the last E(t + dt/2)
+static void refresh_u64(rt_ctx* c, Sys& s) {
+  if (!s.u64_stale) return;
+  PolyTerms V;
+  memset(&V, 0, sizeof(V));
+  const int deg = c->p.taylor_terms - 1;
+  for (int m = 0; m <= deg; ++m) V.v[m] = s.V[m];
+  launch_field_poly(V, deg, c->dstate, 0, s.U, nullptr, nullptr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
+  s.u64_stale = false;
 }
 
-// dK' = dK + R + M + N with M = M_hi + M_lo = (dU_hi + dU_lo) dK, W = dK + M,
-// N = N_hi + N_lo = W (dU_hi + dU_lo)^dagger: four FP32 products, every part
-// kept separately and summed in FP64 (13-function blocks).
+// The reference of a system: K_ref = K of its first kick slot, its traces
+// Tr(K_ref X), and the FP64 part of the step that acts on K_ref:
+//  * constant U: R = sym(cut(cut(U K_ref) U^dagger)) - K_ref;
+//  * field polynomial (U(E) = sum_m E^m V_m): every cut is linear, so
+//    sym(cut(cut(U(E) K_ref) U(E)^dagger)) = sum_p E^p B_p with
+//    B_p = sum_{m+m'=p} sym(cut(cut(V_m K_ref) V_m'^dagger)); B_0 takes -K_ref,
+//    and each step forms R(E) = sum_p E^p B_p by Horner (k_poly_upper).
+// Then dK = K - K_ref for every kick slot whose K changed.
+static void prepare_reference(rt_ctx* c, Sys& s) {
+  const size_t nv = nvals(s, s.pK);
+  if (!s.ref_ready) {
+    materialize(c, s);
+    RT_CUDA_CHECK(cudaMemcpyAsync(s.Kref, s.K[0], sizeof(double2) * nv, cudaMemcpyDeviceToDevice, c->ws));
+    launch_traces(s.Kref, s.pK->nnzb, s.pK->rowidx, s.pK->col, s.d_bsize, s.B, s.S, s.k_to_sT, s.D[0], s.D[1],
+                  s.D[2], s.k_to_hT, s.red_part, c->dstate, 0, c->ring, c->p.obs_capacity, c->n_slots, 0, c->ws,
+                  nullptr, s.tref);
+    s.ref_ready = true;
+    s.r_ready = false;
+  }
+  if (!s.r_ready) {
+    TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
+    TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
+    if (c->p.full_step) {
+      const int deg = c->p.taylor_terms - 1;
+      RT_REQUIRE((int)s.V.size() == deg + 1, RT_ESTATE, "the field polynomial is not formed (call rt_inverse)");
+      RT_REQUIRE(2 * deg < RT_MAX_POLY, RT_EINVAL, "taylor_terms too large for the reference split");
+      if (s.Am.empty())
+        for (int m = 0; m <= deg; ++m) s.Am.push_back(c->arena.get_n<double2>(nvals(s, s.pM)));
+      if (s.Bp.empty())
+        for (int q = 0; q <= 2 * deg; ++q) s.Bp.push_back(c->arena.get_n<double2>(nv));
+      for (double2* b : s.Bp) RT_CUDA_CHECK(cudaMemsetAsync(b, 0, sizeof(double2) * nv, c->ws));
+      for (int m = 0; m <= deg; ++m)
+        gemm(c, s, PC_MISC, tM, false, true, false, false, EPI_STORE, args(s.V[m], s.Kref, s.Am[m]), s.pM);
+      for (int m = 0; m <= deg; ++m)
+        for (int m2 = 0; m2 <= deg; ++m2) {
+          gemm(c, s, PC_MISC, tK, false, true, false, true, EPI_SANDWICH, args(s.Am[m], s.V[m2], s.Rm), s.pK);
+          launch_zaxpy(s.Bp[m + m2], s.Bp[m + m2], s.Rm, 1.0, (int64_t)nv, c->ws);
+        }
+      launch_zaxpy(s.Bp[0], s.Bp[0], s.Kref, -1.0, (int64_t)nv, c->ws);
+    } else {
+      gemm(c, s, PC_MISC, tM, false, true, false, false, EPI_STORE, args(s.U, s.Kref, s.M), s.pM);
+      gemm(c, s, PC_MISC, tK, false, true, false, true, EPI_SANDWICH, args(s.M, s.U, s.Rm), s.pK);
+      launch_zaxpy(s.Rm, s.Rm, s.Kref, -1.0, (int64_t)nv, c->ws);
+    }
+    s.r_ready = true;
+  }
+  for (size_t k = 0; k < s.dk_fresh.size(); ++k) {
+    if (s.dk_fresh[k]) continue;
+    launch_zaxpy(s.dK[k], s.K[k], s.Kref, -1.0, (int64_t)nv, c->ws);
+    s.dk_fresh[k] = 1;
+  }
+}
+
+// The propagator of a reference-split step: dU = U - I stochastically rounded
+// to FP32 (and its block dagger), from the field polynomial at E(t + dt/2)
+// (full step, with R(E) = sum_p E^p B_p in FP64) or from the constant FP64 U.
+static void reference_split_propagator(rt_ctx* c, Sys& s) {
+  if (c->p.full_step) {
+    PolyTerms C;
+    memset(&C, 0, sizeof(C));
+    const int deg2 = 2 * (c->p.taylor_terms - 1);
+    for (int q = 0; q <= deg2; ++q) C.v[q] = s.Bp[q];
+    const double nK = (double)nvals(s, s.pK);
+    run(c, PC_POLY, 0, 16.0 * nK * (deg2 + 2) / 2.0, [&] {  // upper blocks: read B_0..B_deg2, write R
+      launch_poly_upper(C, deg2, c->dstate, 0, s.Rm, s.pK->nnzb, s.pK->rowidx, s.pK->col, s.B, c->ws);
+    });
+    PolyTerms V;
+    memset(&V, 0, sizeof(V));
+    const int deg = c->p.taylor_terms - 1;
+    for (int m = 0; m <= deg; ++m) V.v[m] = s.V[m];
+    const double nU = (double)nvals(s, s.pU);
+    run(c, PC_POLY, 0, 16.0 * nU * (deg + 1) + 16.0 * nU, [&] {  // read V_0..V_deg, write dU and dU^dagger
+      launch_field_poly(V, deg, c->dstate, 0, nullptr, s.dUr, s.dUHr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B,
+                        c->ws, true);
+    });
+    s.u64_stale = true;
+  } else {
+    run(c, PC_MISC, 0, 0, [&] {
+      launch_round_u_sr(s.U, s.dUr, s.dUHr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->dstate, c->ws);
+    });
+  }
+}
+
+// dK' = dK + R + M + N with M = cut(dU dK), W = dK + M, N = cut(W dU^dagger)
+// (FP32 products of the small dK, every part summed in FP64); R in FP64
+// (constant, or R(E) formed for this step's field by the propagator pass).
 static void sandwich_incremental(rt_ctx* c, Sys& s, int kick, int slot) {
   TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
   TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
   double2* dK = s.dK[kick];
   run(c, PC_MISC, 0, 0, [&] { launch_d2f_pad((const double*)dK, (float*)s.Kf, s.pK->nnzb, s.B, true, c->ws); });
-  gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUh, s.Kf, s.Mf), s.pM);
-  TripleInfo tMl = tM;  // the lo halves are precision bookkeeping: no algorithmic flops
-  tMl.true_macs = 0;
-  {
-    GemmArgs g = args(s.dUl, s.Kf, s.Mlo);
-    g.base = dK;       // W = dK + (M_hi + M_lo) from the same epilogue
-    g.addend = s.Mf;
+  if (s.B == 13) {
+    GemmArgs g = args(s.dUr, s.Kf, s.Mf);
+    g.base = dK;  // W = dK + M from the same epilogue
     g.U = s.Wf;
     g.add_map = s.m_to_k;
-    gemm(c, s, PC_UK, tMl, true, true, false, false, EPI_STORE, g, s.pM);
+    gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, g, s.pM);
+  } else {
+    gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUr, s.Kf, s.Mf), s.pM);
+    run(c, PC_MISC, 0, 0, [&] { launch_delta_w(dK, s.m_to_k, s.Mf, s.Wf, s.pM->nnzb, s.B, c->ws); });
   }
-  TripleInfo tKl = tK;
-  tKl.true_macs = 0;
-  gemm(c, s, PC_MUDAG, tKl, true, true, false, false, EPI_STORE, args(s.Wf, s.dUHl, s.Nf), s.pK);
-  GemmArgs g = args(s.Wf, s.dUHh, dK);
+  // 13-function blocks read the pre-transposed dagger; the 4-function kernel
+  // transposes while loading
+  const bool pre_t = s.dUHr != nullptr;
+  GemmArgs g = args(s.Wf, pre_t ? s.dUHr : s.dUr, dK);
   g.herm_max = &c->dstate->herm_bits[slot];
   g.base = dK;
   g.addend = s.Mf;
-  g.addend3 = s.Mlo;
   g.add_map = s.k_to_m;
-  g.base2 = s.Rm[kick];
-  g.addend2 = s.Nf;
-  gemm(c, s, PC_MUDAG, tK, true, true, false, false, EPI_DELTA_SANDWICH, g, s.pK);
+  g.base2 = s.Rm;
+  gemm(c, s, PC_MUDAG, tK, true, true, false, !pre_t, EPI_DELTA_SANDWICH, g, s.pK);
 }
 
 static void enqueue_step(rt_ctx* c) {
@@ -1072,7 +1165,8 @@ static void enqueue_step(rt_ctx* c) {
   int slot = 0;
   for (auto& sp : c->sys) {
     Sys& s = *sp;
-    if (c->p.full_step) build_propagator(c, s, c->p.precision == RT_FP32);
+    if (incremental(c)) reference_split_propagator(c, s);
+    else if (c->p.full_step) build_propagator(c, s, c->p.precision == RT_FP32);
     for (int k = 0; k < c->p.n_kick; ++k) {
       if (incremental(c)) sandwich_incremental(c, s, k, slot + k);
       else sandwich(c, s, k, slot + k);
@@ -1175,6 +1269,7 @@ static void ensure_unitarity_lists(rt_ctx* c, Sys& s) {
 
 static void unitarity(rt_ctx* c, Sys& s, int metric, double* mx, double* mean) {
   ensure_unitarity_lists(c, s);
+  refresh_u64(c, s);
   if (s.duf_current)
     launch_u_from_delta(s.dUf, s.U, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);  // U = I + dU
   if (metric) {
@@ -1281,11 +1376,14 @@ static rt_status guarded(rt_ctx* c, F&& f) {
   }
 }
 
-// Raises RT_ETIMEOUT when a kernel recorded that a bounded wait gave up.
+// Raises RT_ETIMEOUT when a kernel recorded that a bounded wait gave up.  Code
+// 2 (the drain of the copies in flight ran out as well) also marks the context
+// unrecoverable: no checkpoint restore is accepted after it.
 static void check_device_error(rt_ctx* c) {
   int e = 0;
   RT_CUDA_CHECK(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->ws));
   RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+  if (e >= 2) c->unrecoverable = true;
   if (e) throw Error{RT_ETIMEOUT, "a device-side bounded wait gave up (error word " + std::to_string(e) + ")"};
 }
 
@@ -1342,8 +1440,9 @@ rt_status rt_create(rt_ctx** out, const rt_system* sys, int32_t n_sys, const rt_
     RT_REQUIRE(q.hot_step_iters == 0 || (q.hot_fp64_iters >= 1 && q.hot_fp64_iters <= q.hot_step_iters), RT_EINVAL,
                "hot_fp64_iters must be in 1..hot_step_iters");
     RT_REQUIRE((int64_t)n_sys * q.n_kick <= RT_MAX_SLOTS, RT_EINVAL, "too many (system, kick) pairs");
-    RT_REQUIRE(!q.incremental || (q.precision == RT_FP32 && !q.full_step), RT_EINVAL,
-               "the incremental form needs precision RT_FP32 and full_step = 0");
+    RT_REQUIRE(!q.incremental || q.precision == RT_FP32, RT_EINVAL, "the reference split needs precision RT_FP32");
+    RT_REQUIRE(!q.incremental || !q.full_step || (q.field_poly && q.prop == RT_PROP_EM), RT_EINVAL,
+               "the reference split with full_step = 1 needs the EM field polynomial (field_poly = 1)");
     RT_CUDA_CHECK(cudaStreamCreateWithFlags(&c->ws, cudaStreamNonBlocking));
     RT_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     RT_CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
@@ -1451,7 +1550,9 @@ rt_status rt_set_density(rt_ctx* c, int32_t sys, int32_t kick, const double* h) 
     Sys& s = *c->sys[sys];
     const Pattern& P = *s.pK;
     const int B = s.B;
-    if (!s.ref_fresh.empty()) s.ref_fresh[kick] = 0;  // K replaced: the incremental reference is void
+    // K replaced: it is the density again; the reference split keeps K_ref and
+    // carries the new K as dK = K - K_ref from the next step
+    if (!s.dk_fresh.empty()) s.dk_fresh[kick] = 0;
     if (s.n_true == (int64_t)s.n_atoms * B) {
       // no padded atoms: the caller's layout is the device layout; copy directly
       // (a DMA at full speed when the caller's buffer is pinned)
@@ -1486,7 +1587,8 @@ rt_status rt_ground_state(rt_ctx* c, int32_t sys, int32_t order, double mu, doub
     check_sys(c, sys);
     Sys& s = *c->sys[sys];
     RT_REQUIRE(s.sinv_ready, RT_ESTATE, "call rt_inverse first");
-    std::fill(s.ref_fresh.begin(), s.ref_fresh.end(), 0);
+    std::fill(s.dk_fresh.begin(), s.dk_fresh.end(), 0);  // every K replaced, the reference too
+    s.ref_ready = false;
     ground_state(c, s, order, mu, kT, e_lo, e_hi);
     reset_time(c);
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
@@ -1523,14 +1625,12 @@ rt_status rt_propagator(rt_ctx* c, double t) {
     for (auto& sp : c->sys) {
       Sys& s = *sp;
       if (incremental(c)) {
-        // the constant propagator is built in FP64 and carried as FP32 hi + lo
-        materialize(c, s);
+        // the propagator is built in FP64; each step rounds it to FP32
+        // stochastically.  With a constant U the reference part R depends on
+        // U, so a new U drops the reference; with the field polynomial it does not.
         build_propagator(c, s, false);
-        launch_split_u_hilo(s.U, s.dUh, s.dUl, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
-        if (s.dUHh) {
-          launch_dagger32(s.dUh, s.dUHh, s.pU->nnzb, s.B, c->ws);
-          launch_dagger32(s.dUl, s.dUHl, s.pU->nnzb, s.B, c->ws);
-        }
+        if (!c->p.full_step) s.r_ready = false;
+        s.u64_stale = false;
       } else {
         build_propagator(c, s, c->p.precision == RT_FP32);
       }
@@ -1555,11 +1655,8 @@ rt_status rt_step(rt_ctx* c, int32_t n) {
       if (!c->p.full_step) RT_REQUIRE(sp->u_ready, RT_ESTATE, "call rt_propagator first (full_step = 0)");
     }
     if (n == 0) return RT_OK;
-    if (incremental(c)) {
-      for (auto& sp : c->sys)
-        for (int k = 0; k < c->p.n_kick; ++k)
-          if (!sp->ref_fresh[k]) make_reference(c, *sp, k);
-    }
+    if (incremental(c))
+      for (auto& sp : c->sys) prepare_reference(c, *sp);
     if (c->inject & RT_FAULT_WAIT_TIMEOUT_0) {
       // one step, launched directly, with a zero wait budget; the error word
       // is read back here so that this call reports the expiry
@@ -1690,7 +1787,8 @@ rt_status rt_get_matrix(rt_ctx* c, int32_t sys, int32_t kick, int32_t which, dou
     Pattern* P;
     const void* v;
     bool cplx;
-    if (which == RT_MAT_K) materialize(c, s);
+    if (which == RT_MAT_K) materialize(c, s, true);
+    if (which == RT_MAT_U) refresh_u64(c, s);
     if (which == RT_MAT_U && s.duf_current)
       launch_u_from_delta(s.dUf, s.U, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);  // U = I + (U - I)
     matrix_by_id(c, s, kick, which, &P, &v, &cplx);
@@ -1813,7 +1911,10 @@ rt_status rt_get_state(rt_ctx* c, void* buf, size_t* bytes) {
       return RT_OK;
     }
     RT_REQUIRE(*bytes >= need, RT_EINVAL, "state buffer too small");
-    for (auto& sp : c->sys) materialize(c, *sp);  // the state holds K itself
+    for (auto& sp : c->sys) {  // the state holds K and U themselves
+      materialize(c, *sp, true);
+      refresh_u64(c, *sp);
+    }
     for (auto& sp : c->sys) {
       // and U itself: where only U - I is current (FP32 EM, ETRS, M4), U = I + (U - I)
       Sys& s = *sp;
@@ -1850,28 +1951,44 @@ rt_status rt_get_state(rt_ctx* c, void* buf, size_t* bytes) {
 
 rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
   if (!c) return RT_EINVAL;
-  c->poisoned = false;  // restoring a checkpoint clears the poisoned state
-  return guarded(c, [&] {
-    RT_REQUIRE(buf, RT_EINVAL, "NULL state");
-    size_t need = sizeof(StateHeader) + sizeof(DevState) + sizeof(int64_t) * c->n_slots;
-    for (auto& sp : c->sys) {
-      Sys& s = *sp;
-      need += sizeof(double2) * nvals(s, s.pK) * s.K.size() + sizeof(double2) * nvals(s, s.pU);
-      if (s.X) need += sizeof(double2) * nvals(s, s.pU);
-    }
-    RT_REQUIRE(bytes == need, RT_EINVAL, "state size does not match this context");
-    const char* o = (const char*)buf;
-    StateHeader h;
-    memcpy(&h, o, sizeof(h));
-    RT_REQUIRE(h.magic == 0x52544b53544154ull && h.n_slots == c->n_slots, RT_EINVAL, "not a state of this context");
-    o += sizeof(h);
+  // validate the checkpoint before anything else: a rejected restore leaves a
+  // poisoned context poisoned (its K and U may hold a partial step)
+  if (c->unrecoverable) {
+    c->err = "a bounded wait and its drain both gave up: copies may have landed late; the context cannot be restored";
+    return RT_ESTATE;
+  }
+  size_t need = sizeof(StateHeader) + sizeof(DevState) + sizeof(int64_t) * c->n_slots;
+  for (auto& sp : c->sys) {
+    Sys& s = *sp;
+    need += sizeof(double2) * nvals(s, s.pK) * s.K.size() + sizeof(double2) * nvals(s, s.pU);
+    if (s.X) need += sizeof(double2) * nvals(s, s.pU);
+  }
+  if (!buf) {
+    c->err = "NULL state";
+    return RT_EINVAL;
+  }
+  if (bytes != need) {
+    c->err = "state size does not match this context";
+    return RT_EINVAL;
+  }
+  StateHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (h.magic != 0x52544b53544154ull || h.n_slots != c->n_slots) {
+    c->err = "not a state of this context";
+    return RT_EINVAL;
+  }
+  const bool was_poisoned = c->poisoned;
+  c->poisoned = false;
+  rt_status st = guarded(c, [&] {
+    const char* o = (const char*)buf + sizeof(h);
     RT_CUDA_CHECK(cudaMemcpyAsync(c->dstate, o, sizeof(DevState), cudaMemcpyHostToDevice, c->ws));
     o += sizeof(DevState);
     memcpy(c->read_upto.data(), o, sizeof(int64_t) * c->n_slots);
     o += sizeof(int64_t) * c->n_slots;
     for (auto& sp : c->sys) {
       Sys& s = *sp;
-      std::fill(s.ref_fresh.begin(), s.ref_fresh.end(), 0);
+      std::fill(s.dk_fresh.begin(), s.dk_fresh.end(), 0);  // K restored; the reference is kept
+      if (!c->p.full_step) s.r_ready = false;                  // a constant U's R follows the restored U
       for (double2* K : s.K) {
         size_t nb = sizeof(double2) * nvals(s, s.pK);
         RT_CUDA_CHECK(cudaMemcpyAsync(K, o, nb, cudaMemcpyHostToDevice, c->ws));
@@ -1888,13 +2005,7 @@ rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
         launch_u_minus_i_f32(s.U, s.dUf, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
         if (s.dUH) launch_dagger32(s.dUf, s.dUH, s.pU->nnzb, s.B, c->ws);
       }
-      if (s.dUh) {  // incremental form: the FP32 hi + lo parts of the restored U
-        launch_split_u_hilo(s.U, s.dUh, s.dUl, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->ws);
-        if (s.dUHh) {
-          launch_dagger32(s.dUh, s.dUHh, s.pU->nnzb, s.B, c->ws);
-          launch_dagger32(s.dUl, s.dUHl, s.pU->nnzb, s.B, c->ws);
-        }
-      }
+      s.u64_stale = false;  // the restored U is the FP64 propagator (the reference split rounds it per step)
     }
     c->host_step = h.host_step;
     c->t_host = h.t_host;
@@ -1903,6 +2014,8 @@ rt_status rt_set_state(rt_ctx* c, const void* buf, size_t bytes) {
     RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
     return RT_OK;
   });
+  if (st != RT_OK && was_poisoned) c->poisoned = true;  // a failed restore clears nothing
+  return st;
 }
 
 rt_status rt_debug_check(rt_ctx* c, int64_t* n_checked) {

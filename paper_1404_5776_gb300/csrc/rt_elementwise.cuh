@@ -49,8 +49,10 @@ void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const 
                    const double* Dz, const int32_t* kd_map, double* part, const DevState* st, int herm_slot,
                    double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s,
                    const double* ref = nullptr, double* out = nullptr);
-void launch_split_u_hilo(const double2* U, float2* hi, float2* lo, int64_t nnzb, const int32_t* rowidx,
-                         const int32_t* col, int B, cudaStream_t st);
+// dU = U - I stochastically rounded to FP32 (draws keyed on s->step and the element) and its per-block
+// conjugate transpose dUH (if non-null), from an FP64 U
+void launch_round_u_sr(const double2* U, float2* dU, float2* dUH, int64_t nnzb, const int32_t* rowidx,
+                       const int32_t* col, int B, const DevState* s, cudaStream_t st);
 void launch_zaxpy(double2* z, const double2* x, const double2* y, double a, int64_t n, cudaStream_t st);
 void launch_axpy32(float2* z, const float2* x, const float2* y, float a, int64_t n, cudaStream_t st);
 void launch_m4_omega32(const double* T1, const double* T2, const int32_t* u_to_t, const float* C21, const float* C12,
@@ -64,9 +66,14 @@ struct PolyTerms {
   const double2* v[RT_MAX_POLY];
 };
 // U = sum_{m<=deg} E^m V_m at E = s->E[which] (Horner, FP64); writes U (FP64, if non-null) and/or
-// dU = U - I with its per-block conjugate transpose dUH in FP32 (padded rows), if non-null
+// dU = U - I with its per-block conjugate transpose dUH in FP32 (padded rows), if non-null, rounded to
+// nearest or, with `stochastic`, stochastically (draws keyed on s->step and the element)
 void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which, double2* U, float2* dU,
-                       float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st);
+                       float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st,
+                       bool stochastic = false);
+// R = sum_{p<=deg} E^p C_p at E = s->E[which] (Horner, FP64) on the upper blocks of a pattern
+void launch_poly_upper(const PolyTerms& C, int deg, const DevState* s, int which, double2* R, int64_t nnzb,
+                       const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st);
 int launch_unitarity_dev(const double2* E, int64_t nnzb, const int32_t* rowidx, const int32_t* col,
                          const int32_t* bsize, int B, const double* S, const int32_t* us_map, double* part_max,
                          double* part_sum, cudaStream_t st);

@@ -154,11 +154,10 @@ struct GemmArgs {
   const void* addend;
   const int32_t* add_map;   // P_K block -> addend block
   unsigned long long* herm_max;  // max |K_ii - K_ii^dagger| bits
-  const void* base2;        // incremental form: FP64 R at the output block (dense blocks) or null
-  const void* addend2;      // incremental form: FP32 N_lo at the output block (FP32 block layout) or null
-  const void* addend3;      // incremental form: FP32 M_lo through add_map (FP32 block layout) or null
+  const void* base2;        // reference split: FP64 R = U K_ref U^dagger - K_ref at the output block, or null
   const void* zero;         // a zero block (FP32 kernels stage it for missing triples)
-  int* err;                 // device error word (bounded waits that gave up)
+  int* err;                 // device error word: the largest code of a bounded wait that gave up
+                            // (1: wait expired, copies drained; 2: the drain expired too)
   long long wait_ns;        // budget of one bounded wait (FP32 kernels), nanoseconds
 };
 

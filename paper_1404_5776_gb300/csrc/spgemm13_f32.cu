@@ -49,6 +49,11 @@ struct Slot {
   static constexpr int STRIDE = 2 * SB + SKEW;  // elements
 };
 constexpr long long DRAIN_NS = 2000000000ll;  // budget of the drain after a wait gave up (2 s)
+// outcomes of a warp's main loop, also the values of the device error word
+// (the word keeps the largest code any warp recorded)
+constexpr int WAIT_OK = 0;
+constexpr int WAIT_EXPIRED = 1;   // a wait gave up; every copy in flight was drained
+constexpr int DRAIN_EXPIRED = 2;  // the drain gave up as well: copies may still have landed late
 
 __device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 c) {
   c.x = fmaf(a.x, b.x, c.x);
@@ -161,10 +166,11 @@ constexpr int EPT = (NE + 31) / 32;
 // Main loop shared by both kernels: stream the item's triples through the
 // warp's S stages, NT triples per stage (lane group h takes slot h), S - 1
 // groups in flight, and call `mac(sA, sB)` on each staged pair.  Returns
-// false if a wait expired (copies in flight have then been drained, bounded).
+// WAIT_OK, WAIT_EXPIRED (a wait expired; the copies in flight were then
+// drained) or DRAIN_EXPIRED (the drain ran out too: copies may still land).
 // ---------------------------------------------------------------------------
 template <typename V, int NT, int S, typename F>
-__device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* __restrict__ A,
+__device__ __forceinline__ int stream_triples(V* wsm, uint64_t* bar, const V* __restrict__ A,
                                                const V* __restrict__ B, const V* __restrict__ Z,
                                                const int2* __restrict__ ab, int64_t t0, int64_t t1, int lane,
                                                int h, long long wait_ns, F&& mac) {
@@ -196,10 +202,13 @@ __device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* _
     }
     if (!mbar_wait(&bar[stage], (phase >> stage) & 1u, wait_ns)) {
       // bounded drain of every stage with copies in flight (this one included):
-      // no copy may still be landing in shared memory when the warp leaves
+      // no copy may still be landing in shared memory when the warp leaves.
+      // A drain that also runs out leaves copies in flight: reported apart.
+      int code = WAIT_EXPIRED;
       for (int st = 0; st < S; ++st)
-        if ((pending >> st) & 1u) mbar_wait(&bar[st], (phase >> st) & 1u, DRAIN_NS);
-      return false;
+        if ((pending >> st) & 1u)
+          if (!mbar_wait(&bar[st], (phase >> st) & 1u, DRAIN_NS)) code = DRAIN_EXPIRED;
+      return code;
     }
     phase ^= 1u << stage;
     pending &= ~(1u << stage);
@@ -208,7 +217,7 @@ __device__ __forceinline__ bool stream_triples(V* wsm, uint64_t* bar, const V* _
     __syncwarp();  // all lanes done with this stage before it is refilled
     stage = stage + 1 == S ? 0 : stage + 1;
   }
-  return true;
+  return WAIT_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
 #pragma unroll
   for (int r = 0; r < BS; ++r) acc[r] = make_float2(0.f, 0.f);
 
-  const bool ok = stream_triples<float2, NT, C_STAGES>(
+  const int ok = stream_triples<float2, NT, C_STAGES>(
       wsm, bar, static_cast<const float2*>(g.A), static_cast<const float2*>(g.B),
       static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns,
       [&](const float2* sA, const float2* sB) {
@@ -261,8 +270,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
           acc[r] = v;
         }
       });
-  if (!ok) {
-    if (lane == 0 && g.err) atomicExch(g.err, 1);
+  if (ok != WAIT_OK) {
+    if (lane == 0 && g.err) atomicMax(g.err, ok);
     return;
   }
   // partial sums of the two groups to shared memory (every copy has landed)
@@ -304,33 +313,25 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
       if (e < NE) C[(int64_t)q * SB + (e / BS) * RS + e % BS] = sum[k];
     }
     // delta form: also W = K + M in FP32 (K in FP64, dense blocks, through
-    // the map from this pattern to K's; -1 = no K block).  In the incremental
-    // form this is the lo-part product and g.addend holds the hi part:
-    // W = dK + (M_hi + M_lo), summed in FP64.
+    // the map from this pattern to K's; -1 = no K block); in the reference
+    // split K is dK = K - K_ref
     if (g.base) {
       const double2* __restrict__ Kb = static_cast<const double2*>(g.base);
-      const float2* __restrict__ Mh = static_cast<const float2*>(g.addend);
       float2* __restrict__ W = static_cast<float2*>(g.U);
       const int kq = g.add_map ? g.add_map[q] : q;
       double2 kv[EPT];
-      float2 mh[EPT];
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int e = lane + 32 * k;
         kv[k] = make_double2(0.0, 0.0);
-        mh[k] = make_float2(0.f, 0.f);
-        if (e < NE) {
-          if (kq >= 0) kv[k] = Kb[(int64_t)kq * NE + e];
-          if (Mh) mh[k] = Mh[(int64_t)q * SB + (e / BS) * RS + e % BS];
-        }
+        if (e < NE && kq >= 0) kv[k] = Kb[(int64_t)kq * NE + e];
       }
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int e = lane + 32 * k;
         if (e < NE)
           W[(int64_t)q * SB + (e / BS) * RS + e % BS] =
-              make_float2((float)(((double)mh[k].x + (double)sum[k].x) + kv[k].x),
-                          (float)(((double)mh[k].y + (double)sum[k].y) + kv[k].y));
+              make_float2((float)((double)sum[k].x + kv[k].x), (float)((double)sum[k].y + kv[k].y));
       }
     }
   } else if constexpr (EPI == EPI_DELTA_SANDWICH) {
@@ -355,22 +356,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
       }
     }
     if (g.base2) {
-      // incremental form: dK' = dK + R + M_hi + M_lo + N_lo + N_hi, every
-      // part added in FP64 (the lo parts are below FP32 resolution of the hi)
+      // reference split: dK' = dK + R + M + acc with R = U K_ref U^dagger - K_ref
+      // (FP64, this output block)
       const double2* __restrict__ R = static_cast<const double2*>(g.base2);
-      const float2* __restrict__ Nl = static_cast<const float2*>(g.addend2);
-      const float2* __restrict__ Ml = static_cast<const float2*>(g.addend3);
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int e = lane + 32 * k;
         if (e < NE) {
-          const int o = (e / BS) * RS + e % BS;
           const double2 rv = R[(int64_t)q * NE + e];
-          const float2 nl = Nl[(int64_t)q * SB + o];
-          const float2 ml = (aq >= 0) ? Ml[(int64_t)aq * SB + o] : make_float2(0.f, 0.f);
-          val[k] = make_double2(val[k].x + rv.x + (((double)nl.x + (double)ml.x) + (double)sum[k].x),
-                                val[k].y + rv.y + (((double)nl.y + (double)ml.y) + (double)sum[k].y));
-          sum[k] = make_float2(0.f, 0.f);
+          val[k] = make_double2(val[k].x + rv.x, val[k].y + rv.y);
         }
       }
     }
@@ -450,7 +444,7 @@ __global__ void __launch_bounds__(R_WARPS * 32, MINB_R) k_gemm13_r32(GemmArgs g)
 #pragma unroll
   for (int rr = 0; rr < RH; ++rr) acc[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  const bool ok = stream_triples<float, NT, R_STAGES>(
+  const int ok = stream_triples<float, NT, R_STAGES>(
       wsm, bar, static_cast<const float*>(g.A), static_cast<const float*>(g.B), static_cast<const float*>(g.zero),
       g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns, [&](const float* sA, const float* sB) {
         float4 b[BS];  // B[m][4cl .. 4cl+3]
@@ -478,8 +472,8 @@ __global__ void __launch_bounds__(R_WARPS * 32, MINB_R) k_gemm13_r32(GemmArgs g)
           acc[rr] = v;
         }
       });
-  if (!ok) {
-    if (lane == 0 && g.err) atomicExch(g.err, 1);
+  if (ok != WAIT_OK) {
+    if (lane == 0 && g.err) atomicMax(g.err, ok);
     return;
   }
   float* part = wsm;  // [NT][BS][RS]

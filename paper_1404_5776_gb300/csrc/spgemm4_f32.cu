@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_gemm4_f32(GemmArgs g) {
     }
   } else if constexpr (EPI == EPI_DELTA_SANDWICH) {
     if constexpr (sizeof(V) == 8) {
-      // K'_ij = K_ij + M_ij + acc for j >= i (K in FP64); mirror; hermitian diagonal
+      // K'_ij = K_ij (+ R_ij) + M_ij + acc for j >= i (K in FP64); mirror; hermitian diagonal
       const int i = g.rowidx[q], j = g.colidx[q];
       double2* __restrict__ K = static_cast<double2*>(g.C);
       const double2* __restrict__ base = static_cast<const double2*>(g.base) + (int64_t)q * NE;
@@ -138,12 +138,15 @@ __global__ void __launch_bounds__(THREADS, 2) k_gemm4_f32(GemmArgs g) {
 #pragma unroll
         for (int e = 0; e < NE; ++e) mv[e] = make_float2(0.f, 0.f);
       const int qt = g.tmap[q];
+      // reference split: R = U K_ref U^dagger - K_ref (FP64) joins the base
+      const double2* __restrict__ R = g.base2 ? static_cast<const double2*>(g.base2) + (int64_t)q * NE : nullptr;
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int e = r * 4 + c;
-          const double2 kv = base[e];
+          double2 kv = base[e];
+          if (R) kv = make_double2(kv.x + R[e].x, kv.y + R[e].y);
           const double2 v =
               make_double2(kv.x + ((double)mv[e].x + (double)acc[e].x), kv.y + ((double)mv[e].y + (double)acc[e].y));
           K[(int64_t)q * NE + e] = v;

@@ -2,8 +2,13 @@
 x, y and z kicks, advanced together by one rt_step, against the oracle run
 system by system and kick by kick.
 
-Bars: FP64 mode 1e-10 relative on K and on every trace; mixed mode dipole
-within 1e-6 relative to |P| of the FP64 oracle.
+Bars: FP64 mode 1e-10 relative on K and on every trace.  Mixed precision in
+the reference split (the mode that carries the precision claim): the dipole
+along each kick within 1e-6 of its induced swing, max_t |P - P_FP64| /
+max_t |P_FP64(t) - P_FP64(t_1)|.  The literal FP32 path (FP32 products on the
+whole K) is checked at its own, looser level: 1e-6 of |P|, and 3e-4 of the
+induced swing after 10 steps (the cluster's swing is ~20 times smaller than the
+cells'); it does not meet the 1e-6 induced bar.
 """
 import numpy as np
 import pytest
@@ -89,7 +94,8 @@ def test_batched_systems_and_kicks_fp64(rt, systems, prop):
     ctx.close()
 
 
-def test_batched_systems_and_kicks_mixed(rt, systems):
+def test_batched_systems_and_kicks_mixed_literal(rt, systems):
+    """The literal FP32 path, at its own accuracy level (see the module docstring)."""
     steps = 10
     refs = _oracle_runs(systems, steps, "em")
     ctx = _gpu_run(rt, systems, refs, steps, "em", "fp32")
@@ -97,7 +103,39 @@ def test_batched_systems_and_kicks_mixed(rt, systems):
         for d, (_, rows) in enumerate(per_kick):
             obs = ctx.observables(si, d)
             p64 = rows[:, 1 + d].real
-            assert np.abs(obs[:, 3 + 2 * d] - p64).max() <= 1e-6 * np.abs(p64).max(), (si, d)
+            err = np.abs(obs[:, 3 + 2 * d] - p64).max()
+            assert err <= 1e-6 * np.abs(p64).max(), (si, d)
+            assert err <= 3e-4 * np.abs(p64 - p64[0]).max(), (si, d)
             q64 = rows[:, 0].real
             assert np.abs(obs[:, 1] - q64).max() <= 1e-6 * np.abs(q64).max(), (si, d)
+    ctx.close()
+
+
+@pytest.mark.parametrize("full_step", [0, 1])
+def test_batched_reference_split(rt, systems, full_step):
+    """Mixed precision in the reference split for every (system, kick) of the
+    batch (block sizes 13 and 4, the cluster padded from 1 to 4), with U built
+    once (full_step = 0) or from the field polynomial at every step."""
+    steps = 10
+    refs = _oracle_runs(systems, steps, "em")
+    kw = dict(prop="em", precision="fp32", n_kick=3, incremental=1, full_step=full_step)
+    if full_step:
+        kw["field_poly"] = 1
+    ctx = rt.RT(systems, **kw, **_radii())
+    ctx.inverse()
+    for si, (K0, _) in enumerate(refs):
+        for d in range(3):
+            ctx.set_density_dense(si, d, K0)
+            ctx.kick(si, d, d, KAPPA)
+    if not full_step:
+        ctx.propagator(0.0)
+    ctx.step(steps)
+    for si, (_, per_kick) in enumerate(refs):
+        for d, (_, rows) in enumerate(per_kick):
+            obs = ctx.observables(si, d)
+            p64 = rows[:, 1 + d].real
+            err = np.abs(obs[:, 3 + 2 * d] - p64).max()
+            assert err <= 1e-6 * np.abs(p64 - p64[0]).max(), (si, d, full_step)
+            q64 = rows[:, 0].real
+            assert np.abs(obs[:, 1] - q64).max() <= 1e-10 * np.abs(q64).max(), (si, d)
     ctx.close()

@@ -1,9 +1,16 @@
-"""Mixed-precision mode (FP32 block products, FP64 K and reductions) against
-the FP64 oracle.
+"""The literal mixed-precision path (FP32 block products on the whole K, FP64 K
+and reductions) against the FP64 oracle, at its own accuracy level.
 
-Bars (the accuracy targets of the mixed path): dipole Tr(K D_x) within 1e-6
-relative to |P| of the FP64 result, and the S-unitarity error of the mixed
-propagator exceeding the FP64 propagator's by at most 1e-8.
+This path rounds the O(1) density and the propagator to FP32 inside every
+product, and that rounding acts on the dynamics like a small fixed change of
+the Hamiltonian: its dipole error grows with the step count and it does NOT
+meet the mixed-precision bar of 1e-6 of the induced swing (measured on a
+13-function cell: ~1e-6 after 25 steps, ~2e-5 after 500).  The mode that meets
+the bar is the reference split (tests/test_gpu_reference_split.py).  Bars
+here: dipole Tr(K D_x) within 1e-6 relative to |P| of the FP64 result and
+within LITERAL_INDUCED of the induced swing over the tests' short runs, and
+the S-unitarity error of the mixed propagator exceeding the FP64 propagator's
+by at most 1e-8.
 """
 import numpy as np
 import pytest
@@ -12,6 +19,12 @@ import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
+
+LITERAL_INDUCED = 2e-5  # the literal FP32 path over 20-40 steps (not the mixed-precision bar)
+
+
+def _induced_err(p_mixed, p64):
+    return np.abs(p_mixed - p64).max() / np.abs(p64 - p64[0]).max()
 
 
 @pytest.fixture(scope="module")
@@ -56,6 +69,7 @@ def test_mixed_dipole_and_density(rt, basis, prop):
     p64 = rows[:, 1].real
     p32 = obs[:, 3]
     assert np.abs(p32 - p64).max() <= 1e-6 * np.abs(p64).max()
+    assert _induced_err(p32, p64) <= LITERAL_INDUCED
     q64 = rows[:, 0].real
     assert np.abs(obs[:, 1] - q64).max() <= 1e-6 * np.abs(q64).max()
     assert np.abs(Kg - ref.K.val).max() <= 1e-5 * np.abs(ref.K.val).max()
@@ -84,6 +98,7 @@ def test_mixed_field_polynomial(rt, basis):
     rows = np.array([[z for z in ref.step()["obs"]] for _ in range(steps)])
     p64 = rows[:, 1].real
     assert np.abs(obs[:, 3] - p64).max() <= 1e-6 * np.abs(p64).max()
+    assert _induced_err(obs[:, 3], p64) <= LITERAL_INDUCED
     q64 = rows[:, 0].real
     assert np.abs(obs[:, 1] - q64).max() <= 1e-6 * np.abs(q64).max()
 
@@ -119,9 +134,7 @@ def test_mixed_etrs_m4_under_pulse(rt, prop, basis, radii):
     assert np.abs(obs[:, 1] - q64).max() <= 1e-6 * np.abs(q64).max()
     assert np.abs(Kg - ref.K.val).max() <= 1e-5 * np.abs(ref.K.val).max()
     # the pulse drives the z dipole, and the mixed run follows its induced part
-    ind_g = obs[:, 7] - obs[0, 7]
-    ind_r = p64 - p64[0]
-    assert np.abs(ind_g - ind_r).max() <= 1e-3 * np.abs(ind_r).max()
+    assert _induced_err(obs[:, 7], p64) <= LITERAL_INDUCED
 
 
 @pytest.mark.parametrize("prop", ["em", "etrs", "m4"])
@@ -139,11 +152,12 @@ def test_mixed_unitarity_excess(rt, prop):
 
 
 @pytest.mark.parametrize("prop", ["em", "cn"])
-def test_incremental_form_matches_oracle(rt, prop):
-    """Constant propagator (full_step = 0): the incremental form dK = K - K_ref
-    with FP32 products agrees with the FP64 oracle to 1e-6 of the induced dipole
-    amplitude (the strict reading of the dipole error) and 1e-9 of |P|; single
-    elements of K to 1e-8 of max|K|."""
+def test_reference_split_elementwise(rt, prop):
+    """Constant propagator (full_step = 0) in the reference split (dK = K - K_ref
+    with FP32 products): single elements of K within 1e-8 of max|K| of the FP64
+    oracle, mid-run (K = K_ref + dK read back without ending the reference) and
+    at the end; the dipole within 1e-6 of the induced swing and 1e-9 of |P|
+    (the 200-step runs are in test_gpu_reference_split.py)."""
     s = synth.diamond_system(2, "spd13", 6.0, 6.0)
     K0, _, _ = synth.ground_state_dense(s, 2 * s.n_atoms)
     steps = 60
@@ -153,7 +167,7 @@ def test_incremental_form_matches_oracle(rt, prop):
     ctx.kick(0, 0, 0, 1e-3)
     ctx.propagator(0.0)
     ctx.step(steps // 2)
-    Kmid = ctx.matrix(0, rt.RT_MAT_K)  # materialises K_ref + dK; the next step re-bases
+    Kmid = ctx.matrix(0, rt.RT_MAT_K)  # K_ref + dK; the run continues on the same reference
     ctx.step(steps - steps // 2)
     obs = ctx.observables(0, 0)
     Kg = ctx.matrix(0, rt.RT_MAT_K)

@@ -10,6 +10,9 @@ and compared with the literal computation:
 * field polynomial: U(E) = sum_m E^m V_m with V_m = sum_n c_n Q_{n,m},
   Q_{1,0} = T0, Q_{1,1} = -T_D, Q_{n,m} = cut(T0 Q_{n-1,m}) + cut(Q_{1,1} Q_{n-1,m-1}),
   equals the literal truncated series of T(E) at every E.
+* reference split with the field polynomial: with U(E) = sum_m E^m V_m,
+  sym(cut_K(cut_M(U(E) K_ref) U(E)^dagger)) = sum_p E^p B_p,
+  B_p = sum_{m+m'=p} sym(cut_K(cut_M(V_m K_ref) V_m'^dagger)), at every E.
 * ETRS in the delta form (the mixed path): with dU_a = exp(-i dt/2 T(t)) - I,
   dU_b = exp(-i dt/2 T(t+dt)) - I and T(t) = T0 - E(t) T_D,
   I + dU_a + dU_b + cut(dU_b dU_a)  equals  cut(U_b U_a)  from cut(S^-1 H(t)).
@@ -106,11 +109,9 @@ def test_incremental_form_equals_direct_sandwich(setup):
     assert rel(incr.val, direct.val) < 1e-13
 
 
-@pytest.mark.parametrize("terms", [2, 6, 7])
-def test_field_polynomial_equals_literal_series(setup, terms):
+def _field_poly_V(setup, terms, pT, pU, dt=0.05):
+    """V_m of U(E) = sum_m E^m V_m, formed from the oracle's truncated products."""
     s, pats, S, H0, D, Sinv, _ = setup
-    pT, pU = pats[4.0], pats[6.0]
-    dt = 0.05
     T0 = oracle.spgemm(Sinv, H0, pT)
     Q1 = [T0, oracle.BlockMatrix(s.bsize, pT, -oracle.spgemm(Sinv, D, pT).val)]
     deg = terms - 1
@@ -134,13 +135,59 @@ def test_field_polynomial_equals_literal_series(setup, terms):
             cur.append(acc)
             V[m] = oracle.axpy(coef(n), acc, V[m])
         prev = cur
+    return V
+
+
+def _horner(coeffs, E):
+    v = coeffs[-1].val.copy()
+    for c in coeffs[-2::-1]:
+        v = v * E + c.val
+    return v
+
+
+@pytest.mark.parametrize("terms", [2, 6, 7])
+def test_field_polynomial_equals_literal_series(setup, terms):
+    s, pats, S, H0, D, Sinv, _ = setup
+    pT, pU = pats[4.0], pats[6.0]
+    dt = 0.05
+    V = _field_poly_V(setup, terms, pT, pU, dt)
     for E in (0.0, 2e-3, -0.03):
-        poly = V[deg].val.copy()
-        for m in range(deg - 1, -1, -1):
-            poly = poly * E + V[m].val
+        poly = _horner(V, E)
         TE = oracle.spgemm(Sinv, oracle.hamiltonian(H0, D, E), pT)
         U_lit, _ = oracle.taylor_em(TE, dt, terms, pU)
         assert rel(poly, U_lit.val) < 1e-12, (terms, E)
+
+
+@pytest.mark.parametrize("r_K,r_M", [(5.0, 5.0), (5.0, 7.0)])
+def test_reference_part_is_a_polynomial_in_the_field(setup, r_K, r_M):
+    """The FP64 part of the reference split for a field-dependent propagator:
+    the literal sandwich of K_ref with U(E) from the truncated series of
+    T(E) = cut(S^-1 (H0 - E D)) equals sum_p E^p B_p with the B_p formed once
+    from the V_m (every cut is linear)."""
+    s, pats, S, H0, D, Sinv, K0 = setup
+    pT, pU, pK, pM = pats[5.0], pats[6.0], pats[r_K], pats[r_M]
+    dt, terms = 0.05, 6
+    deg = terms - 1
+    V = _field_poly_V(setup, terms, pT, pU, dt)
+    K_ref = oracle.from_dense(s.bsize, pK, K0.astype(complex))
+    A = [oracle.spgemm(Vm, K_ref, pM) for Vm in V]
+    Bp = [oracle.zeros(s.bsize, pK) for _ in range(2 * deg + 1)]
+    cross_only = oracle.zeros(s.bsize, pK)
+    for m in range(deg + 1):
+        for m2 in range(deg + 1):
+            X = oracle.zeros(s.bsize, pK)
+            oracle.spgemm(A[m], V[m2], pK, b_dag=True, upper_only=True, out=X)
+            oracle.mirror_upper(X)
+            Bp[m + m2] = oracle.axpy(1.0, X, Bp[m + m2])
+            if m != m2 and m + m2 == 1:
+                cross_only = oracle.axpy(1.0, X, cross_only)
+    for E in (0.0, 4e-3, -0.05):
+        TE = oracle.spgemm(Sinv, oracle.hamiltonian(H0, D, E), pT)
+        U_lit, _ = oracle.taylor_em(TE, dt, terms, pU)
+        direct = _sandwich_direct(U_lit, K_ref, pM, pK)
+        assert rel(_horner(Bp, E), direct.val) < 1e-12, E
+        if E != 0.0:  # the first-order cross terms carry the field's effect: dropping them is visible
+            assert rel(_horner(Bp, E) - E * cross_only.val, direct.val) > 1e-6
 
 
 PULSE = {"kind": "gaussian", "E0": 0.02, "t0": 0.1, "sigma": 0.2, "omega": 1.1}
