@@ -71,7 +71,6 @@ struct Sys {
   double *T = nullptr, *P0 = nullptr, *P1 = nullptr, *T0 = nullptr, *TD = nullptr, *T2 = nullptr;
   // field polynomial of the EM propagator: U(E) = sum_m E^m V[m]
   std::vector<double2*> V;
-  std::vector<double*> Qa, Qb;  // coefficient matrices of two consecutive powers while V is formed
   double* TDn = nullptr;        // -cut(S^-1 D)
   double2 *U = nullptr, *M = nullptr;
   std::vector<double2*> K;
@@ -95,7 +94,6 @@ struct Sys {
   std::vector<char> dk_fresh;     // per kick: dK holds K - K_ref (K itself is stale)
   bool ref_ready = false;         // K_ref and its traces are formed
   bool r_ready = false;           // R (constant U) or the Bp (field polynomial) match K_ref and U
-  std::vector<double2*> Am;       // cut(V_m K_ref) on P_M while Bp is formed
   std::vector<double2*> Bp;       // coefficients of R(E) on P_K (Bp[0] includes -K_ref)
   float2 *dUr = nullptr, *dUHr = nullptr;  // U - I stochastically rounded to FP32, and its block dagger
   bool u64_stale = false;         // the FP64 U is not formed per step (field polynomial, reference split)
@@ -317,6 +315,27 @@ static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cpl
   run(c, cls, gemm_flops(ti, cplx), gemm_bytes(s, ti, cplx, fp32),
       [&] { launch_gemm(B, fp32, cplx, ad, bd, epi, g, c->ws); });
 }
+
+// Device memory needed only inside one set-up routine: taken from the
+// context's allocator and handed back when the routine ends, once the stream
+// has finished with it (the context's arena keeps everything else until
+// rt_destroy).
+struct Scratch {
+  rt_ctx* c;
+  std::vector<void*> ptrs;
+  explicit Scratch(rt_ctx* ctx) : c(ctx) {}
+  template <typename T>
+  T* get_n(size_t n) {
+    void* p = c->alloc.get(n * sizeof(T) + 16, c->ws);
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Scratch() {
+    if (ptrs.empty()) return;
+    cudaStreamSynchronize(c->ws);
+    for (void* p : ptrs) c->alloc.put(p, c->ws);
+  }
+};
 
 static GemmArgs args(const void* A, const void* B, void* C) {
   GemmArgs g;
@@ -849,10 +868,12 @@ static void build_field_poly(rt_ctx* c, Sys& s) {
     launch_acc_real(s.V[0], s.T0, s.u_to_t, PU->nnzb, s.B, c1, i1, c->ws);
     launch_acc_real(s.V[1], s.TDn, s.u_to_t, PU->nnzb, s.B, c1, i1, c->ws);
   }
-  if (deg >= 2 && s.Qa.empty())
+  Scratch tmp(c);  // coefficient matrices of two consecutive powers while the V_m are formed
+  std::vector<double*> Qa, Qb;
+  if (deg >= 2)
     for (int m = 0; m <= deg; ++m) {
-      s.Qa.push_back(c->arena.get_n<double>(nU));
-      s.Qb.push_back(c->arena.get_n<double>(nU));
+      Qa.push_back(tmp.get_n<double>(nU));
+      Qb.push_back(tmp.get_n<double>(nU));
     }
   TripleInfo& t2 = triples_for(c, s, PT, false, PT, false, PU, false);
   TripleInfo& tn = triples_for(c, s, PT, false, PU, false, PU, false);
@@ -862,7 +883,7 @@ static void build_field_poly(rt_ctx* c, Sys& s) {
     double cn = 0.0;
     int ci = 0;
     taylor_coef(n, p.dt, &cn, &ci);
-    std::vector<double*>& out = (n % 2 == 0) ? s.Qa : s.Qb;
+    std::vector<double*>& out = (n % 2 == 0) ? Qa : Qb;
     for (int m = 0; m <= n; ++m) {
       bool first = true;
       if (m <= n - 1) {
@@ -1073,16 +1094,17 @@ static void prepare_reference(rt_ctx* c, Sys& s) {
       const int deg = c->p.taylor_terms - 1;
       RT_REQUIRE((int)s.V.size() == deg + 1, RT_ESTATE, "the field polynomial is not formed (call rt_inverse)");
       RT_REQUIRE(2 * deg < RT_MAX_POLY, RT_EINVAL, "taylor_terms too large for the reference split");
-      if (s.Am.empty())
-        for (int m = 0; m <= deg; ++m) s.Am.push_back(c->arena.get_n<double2>(nvals(s, s.pM)));
+      Scratch tmp(c);  // cut(V_m K_ref) on P_M while the B_p are formed
+      std::vector<double2*> Am;
+      for (int m = 0; m <= deg; ++m) Am.push_back(tmp.get_n<double2>(nvals(s, s.pM)));
       if (s.Bp.empty())
         for (int q = 0; q <= 2 * deg; ++q) s.Bp.push_back(c->arena.get_n<double2>(nv));
       for (double2* b : s.Bp) RT_CUDA_CHECK(cudaMemsetAsync(b, 0, sizeof(double2) * nv, c->ws));
       for (int m = 0; m <= deg; ++m)
-        gemm(c, s, PC_MISC, tM, false, true, false, false, EPI_STORE, args(s.V[m], s.Kref, s.Am[m]), s.pM);
+        gemm(c, s, PC_MISC, tM, false, true, false, false, EPI_STORE, args(s.V[m], s.Kref, Am[m]), s.pM);
       for (int m = 0; m <= deg; ++m)
         for (int m2 = 0; m2 <= deg; ++m2) {
-          gemm(c, s, PC_MISC, tK, false, true, false, true, EPI_SANDWICH, args(s.Am[m], s.V[m2], s.Rm), s.pK);
+          gemm(c, s, PC_MISC, tK, false, true, false, true, EPI_SANDWICH, args(Am[m], s.V[m2], s.Rm), s.pK);
           launch_zaxpy(s.Bp[m + m2], s.Bp[m + m2], s.Rm, 1.0, (int64_t)nv, c->ws);
         }
       launch_zaxpy(s.Bp[0], s.Bp[0], s.Kref, -1.0, (int64_t)nv, c->ws);
