@@ -692,7 +692,7 @@ void launch_u_from_delta(const float2* dU, double2* U, int64_t nnzb, const int32
 // effect on the induced dipole grows linearly with the step count; rounding
 // each element to one of its two neighbouring floats at random, with the
 // probabilities that make the result unbiased, turns that drift into a random
-// walk.  The uniform draws come from a counter: the SplitMix64 output function
+// walk.  The uniform bits come from a counter: the SplitMix64 output function
 // (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
 // OOPSLA 2014) of a key made of the step number and the element index, so a
 // run is reproducible and a replayed step graph draws fresh numbers.
@@ -703,80 +703,121 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// x rounded to the float f nearest x or to its neighbour g on the other side
-// of x, g with probability (x - f) / (g - f): E[result] = x.
-__device__ __forceinline__ float round_sr(double x, uint64_t key) {
-  const float f = __double2float_rn(x);
-  const double fd = (double)f;
-  if (fd == x || !isfinite(f)) return f;
-  const float g = nextafterf(f, x > fd ? INFINITY : -INFINITY);
-  const double p = (x - fd) / ((double)g - fd);  // in (0, 1/2]
-  const double u = (double)(splitmix64(key) >> 11) * 0x1.0p-53;
-  return u < p ? g : f;
+// x (FP64) stochastically rounded to FP32 with 29 random bits r: adding r to
+// the 29 mantissa bits of x below FP32 precision and cutting them off leaves
+// the float just below |x| or, if the addition carried, the next one up; the
+// carry happens with probability equal to the fraction of a float ulp by which
+// |x| exceeds the lower float, so E[result] = x (the add-and-truncate form of
+// stochastic rounding, Croci et al., "Stochastic rounding: implementation,
+// error analysis and applications", R. Soc. Open Sci. 9, 2022).  The sign bit
+// is untouched (the magnitude is rounded), a carry into the exponent gives the
+// next binade, and the truncated double has 23 mantissa bits, so the final
+// conversion is exact for values in the normal FP32 range.
+__device__ __forceinline__ float round_sr(double x, uint32_t r29) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  b = (b + (r29 & 0x1FFFFFFFu)) & ~0x1FFFFFFFull;
+  return (float)__longlong_as_double((long long)b);
 }
 
-__device__ __forceinline__ uint64_t sr_key(int64_t step, int64_t idx, int part) {
-  return ((uint64_t)step << 32) ^ (uint64_t)(2 * idx + part);
+__device__ __forceinline__ uint64_t sr_bits(int64_t step, int64_t idx) {
+  return splitmix64(((uint64_t)step << 34) ^ (uint64_t)idx);
+}
+
+// Writes one block's FP32 dU (from the FP64 values in v, 32 lanes of a warp
+// over the B*B elements, row-major; rounded to nearest or stochastically) and
+// its conjugate transpose dUH through the warp's shared tile, so that both
+// stores run along rows.
+constexpr int POLY_WARPS = 8;
+__device__ __forceinline__ void store_du_block(float2* __restrict__ tile, double2 v, int e, int B, int rs, int64_t q,
+                                              bool diag, int stochastic, int64_t step, int64_t idx,
+                                              float2* __restrict__ dU) {
+  const int r = e / B, c = e - r * B;
+  const double d = (diag && r == c) ? 1.0 : 0.0;
+  float2 f;
+  if (stochastic) {
+    const uint64_t z = sr_bits(step, idx);
+    f = make_float2(round_sr(v.x - d, (uint32_t)z), round_sr(v.y, (uint32_t)(z >> 32)));
+  } else {
+    f = make_float2((float)(v.x - d), (float)v.y);
+  }
+  dU[q * (int64_t)B * rs + r * rs + c] = f;
+  tile[e] = f;
+}
+
+__device__ __forceinline__ void store_dagger_block(const float2* __restrict__ tile, int lane, int B, int rs, int64_t q,
+                                                  float2* __restrict__ dUH) {
+  const int NE = B * B;
+  for (int e = lane; e < NE; e += 32) {
+    const int r = e / B, c = e - r * B;
+    const float2 t = tile[c * B + r];
+    dUH[q * (int64_t)B * rs + r * rs + c] = make_float2(t.x, -t.y);
+  }
 }
 
 // dU = U - I stochastically rounded to FP32 (FP32 block layout) and its
-// per-block conjugate transpose dUH, from a constant FP64 U; the draws are
-// keyed on the step number held in the device state.
-__global__ void k_round_u_sr(const double2* __restrict__ U, float2* __restrict__ dU, float2* __restrict__ dUH,
-                             int64_t nnzb, const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B,
-                             int rs, const DevState* __restrict__ s) {
+// per-block conjugate transpose dUH, from a constant FP64 U; one warp per
+// block, draws keyed on the step number held in the device state.
+__global__ void __launch_bounds__(POLY_WARPS * 32) k_round_u_sr(const double2* __restrict__ U, float2* __restrict__ dU,
+                                                                float2* __restrict__ dUH, int64_t nnzb,
+                                                                const int32_t* __restrict__ rowidx,
+                                                                const int32_t* __restrict__ col, int B, int rs,
+                                                                const DevState* __restrict__ s) {
+  __shared__ float2 tiles[POLY_WARPS][13 * 13];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t step = s->step;
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t NE = (int64_t)B * B;
-  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = idx / NE;
-    const int e = (int)(idx - q * NE);
-    const int r = e / B, c = e - r * B;
-    const double2 u = U[idx];
-    const double d = (rowidx[q] == col[q] && r == c) ? 1.0 : 0.0;
-    const float2 f = make_float2(round_sr(u.x - d, sr_key(step, idx, 0)), round_sr(u.y, sr_key(step, idx, 1)));
-    dU[q * (int64_t)B * rs + r * rs + c] = f;
-    if (dUH) dUH[q * (int64_t)B * rs + c * rs + r] = make_float2(f.x, -f.y);
+  const int NE = B * B;
+  for (int64_t q = (int64_t)blockIdx.x * POLY_WARPS + warp; q < nnzb; q += (int64_t)gridDim.x * POLY_WARPS) {
+    const bool diag = rowidx[q] == col[q];
+    for (int e = lane; e < NE; e += 32) {
+      const int64_t idx = q * NE + e;
+      store_du_block(tiles[warp], U[idx], e, B, rs, q, diag, 1, step, idx, dU);
+    }
+    __syncwarp();
+    if (dUH) store_dagger_block(tiles[warp], lane, B, rs, q, dUH);
+    __syncwarp();
   }
+}
+
+static int64_t poly_grid(int64_t nnzb) {
+  int64_t g = (nnzb + POLY_WARPS - 1) / POLY_WARPS;
+  return g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g);
 }
 
 void launch_round_u_sr(const double2* U, float2* dU, float2* dUH, int64_t nnzb, const int32_t* rowidx,
                        const int32_t* col, int B, const DevState* s, cudaStream_t st) {
-  int64_t n = nnzb * B * B;
-  if (n == 0) return;
-  int64_t g = (n + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
-  k_round_u_sr<<<(unsigned)g, 256, 0, st>>>(U, dU, dUH, nnzb, rowidx, col, B, rs32(B), s);
+  if (nnzb == 0) return;
+  RT_REQUIRE(B <= 13, RT_EINTERNAL, "block size above 13");
+  k_round_u_sr<<<(unsigned)poly_grid(nnzb), POLY_WARPS * 32, 0, st>>>(U, dU, dUH, nnzb, rowidx, col, B, rs32(B), s);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
 // R = sum_{p<=deg} E^p C_p (Horner, FP64) on the upper blocks (col >= row) of
 // a pattern, E = s->E[which]; the lower blocks of R are not written.
-__global__ void k_poly_upper(PolyTerms C, int deg, const DevState* __restrict__ s, int which, double2* __restrict__ R,
-                             int64_t nnzb, const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col,
-                             int64_t NE) {
+__global__ void __launch_bounds__(POLY_WARPS * 32) k_poly_upper(PolyTerms C, int deg, const DevState* __restrict__ s,
+                                                                int which, double2* __restrict__ R, int64_t nnzb,
+                                                                const int32_t* __restrict__ rowidx,
+                                                                const int32_t* __restrict__ col, int NE) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double E = s->E[which];
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = idx / NE;
-    if (col[q] < rowidx[q]) continue;
-    double2 v = C.v[deg][idx];
-    for (int p = deg - 1; p >= 0; --p) {
-      const double2 cp = C.v[p][idx];
-      v = make_double2(v.x * E + cp.x, v.y * E + cp.y);
+  for (int64_t q = (int64_t)blockIdx.x * POLY_WARPS + warp; q < nnzb; q += (int64_t)gridDim.x * POLY_WARPS) {
+    if (col[q] < rowidx[q]) continue;  // whole warp: lower blocks are not needed
+    for (int e = lane; e < NE; e += 32) {
+      const int64_t idx = q * NE + e;
+      double2 v = C.v[deg][idx];
+      for (int p = deg - 1; p >= 0; --p) {
+        const double2 cp = C.v[p][idx];
+        v = make_double2(fma(v.x, E, cp.x), fma(v.y, E, cp.y));
+      }
+      R[idx] = v;
     }
-    R[idx] = v;
   }
 }
 
 void launch_poly_upper(const PolyTerms& C, int deg, const DevState* s, int which, double2* R, int64_t nnzb,
                        const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st) {
   RT_REQUIRE(deg >= 0 && deg < RT_MAX_POLY, RT_EINTERNAL, "polynomial degree out of range");
-  int64_t n = nnzb * B * B;
-  if (n == 0) return;
-  int64_t g = (n + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
-  k_poly_upper<<<(unsigned)g, 256, 0, st>>>(C, deg, s, which, R, nnzb, rowidx, col, (int64_t)B * B);
+  if (nnzb == 0) return;
+  k_poly_upper<<<(unsigned)poly_grid(nnzb), POLY_WARPS * 32, 0, st>>>(C, deg, s, which, R, nnzb, rowidx, col, B * B);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -881,31 +922,34 @@ void launch_acc_real(double2* V, const double* Q, const int32_t* map, int64_t nn
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
-__global__ void k_field_poly(PolyTerms V, int deg, const DevState* __restrict__ s, int which, double2* __restrict__ U,
-                             float2* __restrict__ dU, float2* __restrict__ dUH, int64_t nnzb,
-                             const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col, int B, int rs,
-                             int stochastic) {
+// U = sum_m E^m V_m by Horner in FP64, one warp per block (coalesced reads of
+// the V_m); FP64 U and/or FP32 dU = U - I with its block dagger dUH.
+__global__ void __launch_bounds__(POLY_WARPS * 32) k_field_poly(PolyTerms V, int deg, const DevState* __restrict__ s,
+                                                                int which, double2* __restrict__ U,
+                                                                float2* __restrict__ dU, float2* __restrict__ dUH,
+                                                                int64_t nnzb, const int32_t* __restrict__ rowidx,
+                                                                const int32_t* __restrict__ col, int B, int rs,
+                                                                int stochastic) {
+  __shared__ float2 tiles[POLY_WARPS][13 * 13];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double E = s->E[which];
   const int64_t step = s->step;
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t NE = (int64_t)B * B;
-  for (; idx < nnzb * NE; idx += (int64_t)gridDim.x * blockDim.x) {
-    double2 u = V.v[deg][idx];
-    for (int m = deg - 1; m >= 0; --m) {
-      const double2 vm = V.v[m][idx];
-      u = make_double2(u.x * E + vm.x, u.y * E + vm.y);
+  const int NE = B * B;
+  for (int64_t q = (int64_t)blockIdx.x * POLY_WARPS + warp; q < nnzb; q += (int64_t)gridDim.x * POLY_WARPS) {
+    const bool diag = rowidx[q] == col[q];
+    for (int e = lane; e < NE; e += 32) {
+      const int64_t idx = q * NE + e;
+      double2 u = V.v[deg][idx];
+      for (int m = deg - 1; m >= 0; --m) {
+        const double2 vm = V.v[m][idx];
+        u = make_double2(fma(u.x, E, vm.x), fma(u.y, E, vm.y));
+      }
+      if (U) U[idx] = u;
+      if (dU) store_du_block(tiles[warp], u, e, B, rs, q, diag, stochastic, step, idx, dU);
     }
-    if (U) U[idx] = u;
-    if (dU) {
-      const int64_t q = idx / NE;
-      const int e = (int)(idx - q * NE);
-      const int r = e / B, c = e - r * B;
-      const double d = (rowidx[q] == col[q] && r == c) ? 1.0 : 0.0;
-      const float2 f = stochastic ? make_float2(round_sr(u.x - d, sr_key(step, idx, 0)), round_sr(u.y, sr_key(step, idx, 1)))
-                                  : make_float2((float)(u.x - d), (float)u.y);
-      dU[q * (int64_t)B * rs + r * rs + c] = f;
-      if (dUH) dUH[q * (int64_t)B * rs + c * rs + r] = make_float2(f.x, -f.y);
-    }
+    __syncwarp();
+    if (dU && dUH) store_dagger_block(tiles[warp], lane, B, rs, q, dUH);
+    __syncwarp();
   }
 }
 
@@ -913,12 +957,10 @@ void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which
                        float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st,
                        bool stochastic) {
   RT_REQUIRE(deg >= 0 && deg < RT_MAX_POLY, RT_EINTERNAL, "field polynomial degree out of range");
-  int64_t n = nnzb * B * B;
-  if (n == 0) return;
-  int64_t g = (n + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
-  k_field_poly<<<(unsigned)g, 256, 0, st>>>(V, deg, s, which, U, dU, dUH, nnzb, rowidx, col, B, rs32(B),
-                                            stochastic ? 1 : 0);
+  RT_REQUIRE(B <= 13, RT_EINTERNAL, "block size above 13");
+  if (nnzb == 0) return;
+  k_field_poly<<<(unsigned)poly_grid(nnzb), POLY_WARPS * 32, 0, st>>>(V, deg, s, which, U, dU, dUH, nnzb, rowidx, col,
+                                                                      B, rs32(B), stochastic ? 1 : 0);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 

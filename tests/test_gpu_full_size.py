@@ -1,11 +1,19 @@
-"""Parity at the benchmark's size (4096 atoms x 13 functions, r = 8 A, the
-launch configuration bench.py times), on sampled outputs the oracle computes
-row by row: the library builds U and steps a seeded hermitian K once; the
-oracle recomputes sampled rows of M = cut(U K) and of the upper blocks of
+"""Parity at the benchmark's size (4096 atoms x 13 functions), on sampled
+outputs the oracle computes row by row.
+
+Sandwich (r = 8 A): the library builds U and steps a seeded hermitian K once;
+the oracle recomputes sampled rows of M = cut(U K) and of the upper blocks of
 K' = cut(M U^dagger) from the library's own U and K (its truncated product
 restricted to those rows), and the two are compared block by block.  FP64 at
 1e-10 relative; the mixed path (FP32 block products in the delta form) at
-1e-6 of the largest block entry of the sampled rows."""
+1e-6 of the largest block entry of the sampled rows.
+
+Taylor powers (r = 8 and 10 A, the radius the benchmark headlines): from the
+library's own T = cut(S^-1 H), the oracle forms the full truncated powers
+T^2, T^3, T^4 and sampled rows of T^5 and of U = sum_n (-i dt)^n T^n / n!
+(eq. matrix_exp, six terms); the library's U on those rows is compared with
+them, U - I at 1e-10 of its largest entry in FP64, and at 1e-6 in the literal
+mixed path, whose powers are the FP32 real block products (k_gemm13_r32)."""
 import numpy as np
 import pytest
 
@@ -46,6 +54,52 @@ def workload():
     vals[lower] = np.conj(np.transpose(vals[tq[lower]], (0, 2, 1)))
     Kb = oracle.BlockMatrix(s.bsize, pat, vals.reshape(-1))
     return s, pat, Kb
+
+
+@pytest.fixture(scope="module")
+def cell4096():
+    return synth.diamond_system(8, "spd13", 7.0, 7.0)
+
+
+@pytest.mark.parametrize("radius", [8.0, 10.0])
+def test_taylor_powers_rows_at_full_size(rt, cell4096, radius):
+    s = cell4096
+    radii = dict(r_Sinv=radius, r_T=radius, r_U=radius, r_K=radius, r_M=radius)
+    got = {}
+    T = None
+    for precision in ("fp64", "fp32"):
+        ctx = rt.RT(s, precision=precision, full_step=0, dt=0.05, **radii)
+        ctx.inverse()
+        ctx.propagator(0.0)
+        if T is None:
+            T = ctx.matrix(0, rt.RT_MAT_T)
+            rpT, colT = ctx.pattern(0, rt.RT_PAT_T)
+            rpU, colU = ctx.pattern(0, rt.RT_PAT_U)
+        got[precision] = ctx.matrix(0, rt.RT_MAT_U)
+        ctx.close()
+    pT, pU = oracle.Pattern(rpT, colT), oracle.Pattern(rpU, colU)
+    assert pT == oracle.pattern(s.pos, s.cell, radius)  # the patterns themselves are pinned bit for bit
+    Tb = oracle.BlockMatrix(s.bsize, pT, T)
+    dt = 0.05
+    coef = [(-1j * dt) ** n / np.prod(np.arange(1, n + 1)) for n in range(6)]
+    P = oracle.restrict(Tb, pU)
+    Uo = oracle.axpy(coef[1], P, oracle.identity(s.bsize, pU))
+    for n in range(2, 5):  # full powers: row i of T^5 needs rows of T^4 over the 4-hop neighbourhood
+        P = oracle.spgemm(Tb, P, pU)
+        Uo = oracle.axpy(coef[n], P, Uo)
+    P5 = oracle.zeros(s.bsize, pU)
+    for i in SAMPLE:
+        oracle.spgemm(Tb, P, pU, rows=(i, i + 1), out=P5)
+    Uo = oracle.axpy(coef[5], P5, Uo)
+    ident = oracle.identity(s.bsize, pU).val
+    for precision, bar in (("fp64", 1e-10), ("fp32", 1e-6)):
+        worst, scale = 0.0, 0.0
+        for i in SAMPLE:
+            sl = slice(Uo.voff[pU.rowptr[i]], Uo.voff[pU.rowptr[i + 1]])
+            ref = Uo.val[sl] - ident[sl]
+            worst = max(worst, float(np.abs(got[precision][sl] - ident[sl] - ref).max()))
+            scale = max(scale, float(np.abs(ref).max()))
+        assert worst <= bar * scale, (precision, radius, worst, scale)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
