@@ -67,6 +67,8 @@ def parse():
                     help="run only the mixed-precision context (FOE ground state, kick, warm-up, steps) and print "
                          "its per-kernel-class times: a small resident set for kernel captures, no benchmark line")
     ap.add_argument("--literal", action="store_true", help="--kernel-case: the literal FP32 path")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="FP32 contexts run the sandwich's 13-function products on the tensor cores (tcgen05)")
     ap.add_argument("--study", default=None, choices=["truncation", "scaling", "batching", "propagators",
                                                        "propagator-timing"],
                     help="run a study instead of the benchmark and print its JSON line")
@@ -277,7 +279,8 @@ def run_gpu(args):
     mu, e_lo, e_hi = model_spectrum(args)
     R = args.radius
     radii = dict(r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
-    common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=8192, **radii)
+    common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=8192, tensor_cores=1 if args.tensor_cores else 0,
+                  **radii)
     split_ok = args.prop == "em" and args.basis in ("spd13", "sp4")
 
     # --- FP64 context (the plain FP64 GPU path): ground state (untimed set-up), kick
@@ -791,7 +794,7 @@ def kernel_case(args):
     s = workload(args)
     mu, e_lo, e_hi = model_spectrum(args)
     R = args.radius
-    kw = dict(precision="fp32")
+    kw = dict(precision="fp32", tensor_cores=1 if args.tensor_cores else 0)
     if not args.literal and args.prop == "em":
         kw.update(incremental=1, field_poly=1)
     ctx = rtm.RT(s, dt=0.05, prop=args.prop, obs_capacity=args.steps + args.warmup + 8,

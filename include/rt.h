@@ -188,6 +188,16 @@ typedef struct {
                                run as FP32 block products (Hotelling converges
                                quadratically: an FP64 iteration squares the FP32
                                error away).  1..hot_step_iters; default 1       */
+  int32_t tensor_cores;     /* with RT_FP32, 1: the sandwich's complex products of
+                               13-function blocks (M = dU K, K' = W dU^dagger)
+                               run on the tensor cores (tcgen05, TF32 parts and
+                               FP32 remainders of both operands, three MMAs per
+                               K step, the partial sum of every k added in FP32
+                               registers).  Agrees with the CUDA cores to FP32
+                               level per step, but the tensor cores' own
+                               accumulation is coarser than round-to-nearest
+                               FP32 and its error adds up coherently over long
+                               runs; 0 (default): FP32 CUDA cores              */
 } rt_params;
 
 typedef struct {
@@ -199,7 +209,7 @@ typedef struct {
 /* Fills the defaults: radii 8 A, dt 0.05, EM, 6 Taylor terms, tol 1e-10,
  * maxit 100, 2 CN iterations per step, FP64, full step, 1 kick, 12 kick terms,
  * 4096 observable steps, graphs on, incremental form and field polynomial off,
- * 1 FP64 CN iteration per step in the mixed mode. */
+ * 1 FP64 CN iteration per step in the mixed mode, CUDA-core FP32 products. */
 RT_API rt_status rt_default_params(rt_params* p);
 
 /* Creates a context for n_sys systems: validates and copies the host inputs,

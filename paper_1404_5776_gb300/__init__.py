@@ -58,7 +58,8 @@ class rt_params(ctypes.Structure):
                 ("hot_maxit", ctypes.c_int32), ("hot_step_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("full_step", ctypes.c_int32), ("n_kick", ctypes.c_int32), ("kick_terms", ctypes.c_int32),
                 ("obs_capacity", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("incremental", ctypes.c_int32),
-                ("field_poly", ctypes.c_int32), ("hot_fp64_iters", ctypes.c_int32)]
+                ("field_poly", ctypes.c_int32), ("hot_fp64_iters", ctypes.c_int32),
+                ("tensor_cores", ctypes.c_int32)]
 
 
 class rt_field(ctypes.Structure):

@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librtdm.so")
-SOURCES = ["patterns.cu", "spgemm.cu", "spgemm13_f32.cu", "spgemm4_f32.cu", "elementwise.cu", "rt_api.cu", "noalloc.cu",
-           "rt_check.cu"]
+SOURCES = ["patterns.cu", "spgemm.cu", "spgemm13_f32.cu", "spgemm13_tc.cu", "spgemm4_f32.cu", "elementwise.cu",
+           "rt_api.cu", "noalloc.cu", "rt_check.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

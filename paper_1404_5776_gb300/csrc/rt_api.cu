@@ -44,6 +44,7 @@ struct TripleKey {
 
 struct TripleInfo {
   Triples t;
+  TileList tiles;  // row tiles for the tensor-core kernel (built for the sandwich's FP32 13-function products)
   int64_t true_macs = 0;
   int64_t nnzb_a = 0, nnzb_b = 0;
   int64_t true_elems_a = 0, true_elems_b = 0, true_elems_c = 0;
@@ -312,6 +313,16 @@ static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cpl
                "block product accumulator overlaps an operand");
   }
   int B = s.B;
+  if (fp32 && cplx && B == 13 && !ad && !bd && ti.tiles.built && (epi == EPI_STORE || epi == EPI_DELTA_SANDWICH)) {
+    g.tl_n = ti.tiles.n_tiles;
+    g.tl_item0 = ti.tiles.item0;
+    g.tl_nitem = ti.tiles.nitem;
+    g.tl_uptr = ti.tiles.uptr;
+    g.tl_ua = ti.tiles.ua;
+    g.tl_ub = ti.tiles.ub;
+    run(c, cls, gemm_flops(ti, cplx), gemm_bytes(s, ti, cplx, fp32), [&] { launch_gemm13_tc(epi, g, c->ws); });
+    return;
+  }
   run(c, cls, gemm_flops(ti, cplx), gemm_bytes(s, ti, cplx, fp32),
       [&] { launch_gemm(B, fp32, cplx, ad, bd, epi, g, c->ws); });
 }
@@ -507,6 +518,13 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
     triples_for(c, s, s.pA, false, s.pU, false, s.pU, false);  // A X
     triples_for(c, s, s.pU, false, s.pU, false, s.pU, false);  // X Z
     triples_for(c, s, s.pU, false, s.pA, false, s.pU, false);  // X B
+  }
+  if (p.precision == RT_FP32 && s.B == 13 && p.tensor_cores) {
+    // row tiles of the sandwich's two complex products for the tensor-core kernel
+    TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
+    build_tiles(tM.tiles, tM.t, *s.pM, c->arena, c->ws);
+    TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
+    build_tiles(tK.tiles, tK.t, *s.pK, c->arena, c->ws);
   }
   if (p.precision == RT_FP32) {
     RT_REQUIRE(p.r_M >= p.r_K, RT_EINVAL, "the FP32 delta-form sandwich needs r_M >= r_K");
@@ -1427,6 +1445,7 @@ rt_status rt_default_params(rt_params* p) {
   p->hot_maxit = 100;
   p->hot_step_iters = 2;
   p->hot_fp64_iters = 1;
+  p->tensor_cores = 0;
   p->precision = RT_FP64;
   p->full_step = 1;
   p->n_kick = 1;

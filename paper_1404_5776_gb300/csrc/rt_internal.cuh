@@ -93,6 +93,23 @@ struct Triples {
   int2* ab = nullptr;           // [n_triples] (a block, b block)
 };
 
+// Row tiles of a triple list for the tensor-core products: up to TC_TILE
+// consecutive items of one output block row; per tile the merged, ascending
+// list of the A blocks its items use (one "entry" per distinct A block, i.e.
+// per k of the row), with the B block each item multiplies it by (-1: the
+// item has no triple with that k).
+constexpr int TC_TILE = 8;
+struct TileList {
+  bool built = false;
+  int64_t n_tiles = 0;
+  int64_t n_entries = 0;
+  int32_t* item0 = nullptr;  // [n_tiles] first item of the tile
+  int32_t* nitem = nullptr;  // [n_tiles] items in the tile (1..TC_TILE)
+  int64_t* uptr = nullptr;   // [n_tiles+1] entry range
+  int32_t* ua = nullptr;     // [n_entries] A block of the entry
+  int32_t* ub = nullptr;     // [n_entries][TC_TILE] B block per item slot, -1 = none
+};
+
 // Build P_r on the device (cell lists, minimum image, FP64 without contraction).
 void build_pattern(Pattern& P, int n_atoms, const double* d_pos, const double* cell, double r,
                    Arena& arena, cudaStream_t st);
@@ -106,6 +123,10 @@ void build_triples(Triples& T, const Pattern& A, bool a_dag, const Pattern& B, b
 void build_block_map(int32_t* map, const Pattern& src, const Pattern& dst, cudaStream_t st);
 // map[q] = index in `dst` of the transpose (j,i) of block q=(i,j) of `src` (or -1).
 void build_transpose_map(int32_t* map, const Pattern& src, const Pattern& dst, cudaStream_t st);
+
+// Row tiles of a triple list whose items are the blocks of P_C (or its upper
+// blocks) in increasing order, each item's triples in increasing A block.
+void build_tiles(TileList& tl, const Triples& T, const Pattern& C, Arena& arena, cudaStream_t st);
 
 // exclusive scan of int64 counts (n+1 outputs, out[n] = total); returns total
 int64_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Arena& arena, cudaStream_t st);
@@ -159,12 +180,25 @@ struct GemmArgs {
   int* err;                 // device error word: the largest code of a bounded wait that gave up
                             // (1: wait expired, copies drained; 2: the drain expired too)
   long long wait_ns;        // budget of one bounded wait (FP32 kernels), nanoseconds
+  // row tiles (tensor-core products)
+  int64_t tl_n;
+  const int32_t* tl_item0;
+  const int32_t* tl_nitem;
+  const int64_t* tl_uptr;
+  const int32_t* tl_ua;
+  const int32_t* tl_ub;
 };
 
 // Row stride of an FP32 block: 13-function blocks are padded to 13 x 16
 // (16-byte aligned rows, the shared-memory layout of the FP32 kernels).
 inline int rs32(int B) { return B == 13 ? 16 : B; }
 inline int sb32(int B) { return B * rs32(B); }
+
+// Complex 13-function FP32 products on the tensor cores (tcgen05, 3xTF32 split,
+// FP32 accumulation of per-k partial sums) over row tiles (g.tl_*), with the
+// epilogues EPI_STORE (and W = K + M) and EPI_DELTA_SANDWICH; false if `epi`
+// is not one of them.
+bool launch_gemm13_tc(Epilogue epi, const GemmArgs& g, cudaStream_t st);
 
 // Launches; `cplx` selects complex values, `b_dag` conj-transposes B's blocks,
 // `a_dag` A's blocks.  Element type by precision: FP64 double/double2, FP32 float/float2.

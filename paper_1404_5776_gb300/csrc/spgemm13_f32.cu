@@ -25,6 +25,7 @@
 //     by default, read from the global timer): on expiry the kernel records an
 //     error code, waits (bounded) for its copies in flight and returns.
 #include "rt_internal.cuh"
+#include "rt_ptx.cuh"
 
 namespace rt {
 
@@ -65,54 +66,6 @@ __device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 c) {
 
 __device__ __forceinline__ void amax_nonneg(unsigned long long* p, double v) {
   atomicMax(p, (unsigned long long)__double_as_longlong(v));
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void tma_load_1d(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_u32(sdst)),
-      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Wait for the phase with the given parity, at most budget_ns nanoseconds of
-// the global timer (and at most 2^30 polls); false on expiry.  A budget of 0
-// gives up at once (host-side fault injection of a wait that expires).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long budget_ns) {
-  if (budget_ns <= 0) return false;
-  const unsigned addr = smem_u32(bar);
-  if (mbar_try(addr, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (unsigned it = 1; it < (1u << 30); ++it) {
-    if (mbar_try(addr, parity)) return true;
-    if ((it & 63u) == 0u && (long long)(global_ns() - t0) > budget_ns) return false;
-  }
-  return false;
 }
 
 // Issue the TMA copies of one group of NT triples into `buf` (slot k holds A

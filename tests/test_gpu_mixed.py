@@ -187,3 +187,37 @@ def test_reference_split_elementwise(rt, prop):
     assert err <= 1e-8 * np.abs(p64).max()
     assert err <= 1e-6 * np.abs(p64 - p64[0]).max()
     assert np.abs(Kg - ref.K.val).max() <= 5e-8 * np.abs(ref.K.val).max()
+
+
+@pytest.mark.parametrize("incremental", [0, 1])
+def test_tensor_core_and_cuda_core_products_agree(rt, incremental):
+    """The sandwich's complex 13-function products on the tensor cores (tcgen05,
+    3xTF32 with per-k partial sums added in FP32) against the FP32 CUDA-core
+    kernels and the FP64 oracle: K after 10 steps, element by element, within
+    2e-6 of max|K| between the two FP32 paths (the literal path, FP32 products on
+    the whole K) or 2e-8 (the reference split, FP32 products on dK), and the
+    dipole within 1e-6 of |P| of the oracle."""
+    s = synth.diamond_system(2, "spd13", 6.0, 6.0)
+    K0, _, _ = synth.ground_state_dense(s, 2 * s.n_atoms)
+    steps = 10
+    got = {}
+    for tc in (0, 1):
+        kw = dict(prop="em", precision="fp32", tensor_cores=tc)
+        if incremental:
+            kw.update(incremental=1, field_poly=1)
+        ctx = rt.RT(s, **kw, **_radii(6.0))
+        ctx.inverse()
+        ctx.set_density_dense(0, 0, K0)
+        ctx.kick(0, 0, 0, 1e-3)
+        ctx.step(steps)
+        got[tc] = (ctx.matrix(0, rt.RT_MAT_K), ctx.observables(0, 0))
+        ctx.close()
+    ref = oracle.Propagator(s, oracle.Params(prop="em", **_radii(6.0)))
+    ref.set_density_dense(K0)
+    ref.kick(0, 1e-3)
+    p64 = np.array([ref.step()["obs"][1].real for _ in range(steps)])
+    scale = np.abs(got[0][0]).max()
+    assert np.abs(got[1][0] - got[0][0]).max() <= (2e-8 if incremental else 2e-6) * scale
+    for tc in (0, 1):
+        assert np.abs(got[tc][1][:, 3] - p64).max() <= 1e-6 * np.abs(p64).max()
+        assert np.abs(got[tc][0] - ref.K.val).max() <= 1e-5 * np.abs(ref.K.val).max()
