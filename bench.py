@@ -606,7 +606,8 @@ def precision_study(args):
     mu, e_lo, e_hi = model_spectrum(args)
     R = args.radius
     n = args.precision_study
-    common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=n + 8, r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
+    common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=n + 8, r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R,
+                  tensor_cores=1 if args.tensor_cores else 0)
     c64 = rtm.RT(s, precision="fp64", **common)
     c64.inverse()
     c64.ground_state(0, args.foe_order, mu, 0.01, e_lo, e_hi)
