@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--radius", type=float, default=10.0)
     ap.add_argument("--ncell", type=int, default=8)
     ap.add_argument("--basis", default="spd13")
+    ap.add_argument("--atom-order", default="lattice", choices=["lattice", "morton"],
+                    help="numbering of the atoms of the benchmark cell (morton: along a Morton curve)")
     ap.add_argument("--prop", default="em", choices=["em", "cn", "etrs", "m4"])
     ap.add_argument("--foe-order", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -67,6 +69,8 @@ def parse():
                     help="run only the mixed-precision context (FOE ground state, kick, warm-up, steps) and print "
                          "its per-kernel-class times: a small resident set for kernel captures, no benchmark line")
     ap.add_argument("--literal", action="store_true", help="--kernel-case: the literal FP32 path")
+    ap.add_argument("--packed-fma", action="store_true",
+                    help="reference split: the complex products with packed two-lane FMAs (column-planar U - I and W)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="FP32 contexts run the sandwich's 13-function products on the tensor cores (tcgen05)")
     ap.add_argument("--study", default=None, choices=["truncation", "scaling", "batching", "propagators",
@@ -79,7 +83,7 @@ def parse():
 
 def workload(args):
     import synth
-    s = synth.diamond_system(args.ncell, args.basis, 7.0, 7.0)
+    s = synth.diamond_system(args.ncell, args.basis, 7.0, 7.0, order=args.atom_order)
     return s
 
 
@@ -96,7 +100,8 @@ def model_spectrum(args):
 
 def cfg_name(args):
     return (f"diamond {args.ncell ** 3 * 8} atoms x {synth_nfunc(args.basis)} functions, r_S=r_H=7A, "
-            f"r_Sinv=r_T=r_U=r_K=r_M={args.radius:g}A, dt=0.05, {args.prop.upper()} 6 terms, x-kick 1e-3")
+            f"r_Sinv=r_T=r_U=r_K=r_M={args.radius:g}A, dt=0.05, {args.prop.upper()} 6 terms, x-kick 1e-3"
+            + (", atoms in Morton order" if args.atom_order == "morton" else ""))
 
 
 def synth_nfunc(basis):
@@ -280,7 +285,7 @@ def run_gpu(args):
     R = args.radius
     radii = dict(r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
     common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=8192, tensor_cores=1 if args.tensor_cores else 0,
-                  **radii)
+                  packed_fma=1 if args.packed_fma else 0, **radii)
     split_ok = args.prop == "em" and args.basis in ("spd13", "sp4")
 
     # --- FP64 context (the plain FP64 GPU path): ground state (untimed set-up), kick
@@ -607,7 +612,7 @@ def precision_study(args):
     R = args.radius
     n = args.precision_study
     common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=n + 8, r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R,
-                  tensor_cores=1 if args.tensor_cores else 0)
+                  tensor_cores=1 if args.tensor_cores else 0, packed_fma=1 if args.packed_fma else 0)
     c64 = rtm.RT(s, precision="fp64", **common)
     c64.inverse()
     c64.ground_state(0, args.foe_order, mu, 0.01, e_lo, e_hi)
@@ -795,7 +800,7 @@ def kernel_case(args):
     s = workload(args)
     mu, e_lo, e_hi = model_spectrum(args)
     R = args.radius
-    kw = dict(precision="fp32", tensor_cores=1 if args.tensor_cores else 0)
+    kw = dict(precision="fp32", tensor_cores=1 if args.tensor_cores else 0, packed_fma=1 if args.packed_fma else 0)
     if not args.literal and args.prop == "em":
         kw.update(incremental=1, field_poly=1)
     ctx = rtm.RT(s, dt=0.05, prop=args.prop, obs_capacity=args.steps + args.warmup + 8,

@@ -198,6 +198,13 @@ typedef struct {
                                accumulation is coarser than round-to-nearest
                                FP32 and its error adds up coherently over long
                                runs; 0 (default): FP32 CUDA cores              */
+  int32_t packed_fma;       /* reference split (incremental = 1) on the CUDA
+                               cores with 13-function blocks: 1 keeps U - I and
+                               W = dK + M column-planar and runs the complex
+                               products with packed two-lane FMAs
+                               (fma.rn.f32x2, rows in pairs); 0 (default): the
+                               row-layout kernel with scalar FMAs.  Same sums,
+                               in a different order                            */
 } rt_params;
 
 typedef struct {

@@ -59,7 +59,8 @@ class rt_params(ctypes.Structure):
                 ("full_step", ctypes.c_int32), ("n_kick", ctypes.c_int32), ("kick_terms", ctypes.c_int32),
                 ("obs_capacity", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("incremental", ctypes.c_int32),
                 ("field_poly", ctypes.c_int32), ("hot_fp64_iters", ctypes.c_int32),
-                ("tensor_cores", ctypes.c_int32)]
+                ("tensor_cores", ctypes.c_int32),
+                ("packed_fma", ctypes.c_int32)]
 
 
 class rt_field(ctypes.Structure):

@@ -740,8 +740,27 @@ __device__ __forceinline__ void store_du_block(float2* __restrict__ tile, double
   } else {
     f = make_float2((float)(v.x - d), (float)v.y);
   }
-  dU[q * (int64_t)B * rs + r * rs + c] = f;
+  if (dU) dU[q * (int64_t)B * rs + r * rs + c] = f;
   tile[e] = f;
+}
+
+// The block in the tile written column-planar (13-function blocks, 416
+// floats: for each column m the real parts of rows 0..15, then the
+// imaginary parts; rows 13..15 zero), the A layout of the packed FP32
+// product kernel; coalesced stores.
+__device__ __forceinline__ void store_planar_block(const float2* __restrict__ tile, int lane, int64_t q,
+                                                   float2* __restrict__ dU) {
+  constexpr int B = 13, RS = 16;
+  float* __restrict__ D = reinterpret_cast<float*>(dU) + q * (int64_t)(2 * B * RS);
+  for (int idx = lane; idx < 2 * B * RS; idx += 32) {
+    const int m = idx / (2 * RS), w = idx % (2 * RS), r = w % RS;
+    float v = 0.f;
+    if (r < B) {
+      const float2 t = tile[r * B + m];
+      v = w >= RS ? t.y : t.x;
+    }
+    D[idx] = v;
+  }
 }
 
 __device__ __forceinline__ void store_dagger_block(const float2* __restrict__ tile, int lane, int B, int rs, int64_t q,
@@ -761,7 +780,7 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) k_round_u_sr(const double2* _
                                                                 float2* __restrict__ dUH, int64_t nnzb,
                                                                 const int32_t* __restrict__ rowidx,
                                                                 const int32_t* __restrict__ col, int B, int rs,
-                                                                const DevState* __restrict__ s) {
+                                                                const DevState* __restrict__ s, int planar) {
   __shared__ float2 tiles[POLY_WARPS][13 * 13];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t step = s->step;
@@ -770,9 +789,10 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) k_round_u_sr(const double2* _
     const bool diag = rowidx[q] == col[q];
     for (int e = lane; e < NE; e += 32) {
       const int64_t idx = q * NE + e;
-      store_du_block(tiles[warp], U[idx], e, B, rs, q, diag, 1, step, idx, dU);
+      store_du_block(tiles[warp], U[idx], e, B, rs, q, diag, 1, step, idx, planar ? nullptr : dU);
     }
     __syncwarp();
+    if (planar) store_planar_block(tiles[warp], lane, q, dU);
     if (dUH) store_dagger_block(tiles[warp], lane, B, rs, q, dUH);
     __syncwarp();
   }
@@ -784,10 +804,12 @@ static int64_t poly_grid(int64_t nnzb) {
 }
 
 void launch_round_u_sr(const double2* U, float2* dU, float2* dUH, int64_t nnzb, const int32_t* rowidx,
-                       const int32_t* col, int B, const DevState* s, cudaStream_t st) {
+                       const int32_t* col, int B, const DevState* s, cudaStream_t st, bool planar) {
   if (nnzb == 0) return;
   RT_REQUIRE(B <= 13, RT_EINTERNAL, "block size above 13");
-  k_round_u_sr<<<(unsigned)poly_grid(nnzb), POLY_WARPS * 32, 0, st>>>(U, dU, dUH, nnzb, rowidx, col, B, rs32(B), s);
+  RT_REQUIRE(!planar || B == 13, RT_EINTERNAL, "column-planar blocks are 13-function blocks");
+  k_round_u_sr<<<(unsigned)poly_grid(nnzb), POLY_WARPS * 32, 0, st>>>(U, dU, dUH, nnzb, rowidx, col, B, rs32(B), s,
+                                                                      planar ? 1 : 0);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -929,7 +951,7 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) k_field_poly(PolyTerms V, int
                                                                 float2* __restrict__ dU, float2* __restrict__ dUH,
                                                                 int64_t nnzb, const int32_t* __restrict__ rowidx,
                                                                 const int32_t* __restrict__ col, int B, int rs,
-                                                                int stochastic) {
+                                                                int stochastic, int planar) {
   __shared__ float2 tiles[POLY_WARPS][13 * 13];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double E = s->E[which];
@@ -945,9 +967,10 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) k_field_poly(PolyTerms V, int
         u = make_double2(fma(u.x, E, vm.x), fma(u.y, E, vm.y));
       }
       if (U) U[idx] = u;
-      if (dU) store_du_block(tiles[warp], u, e, B, rs, q, diag, stochastic, step, idx, dU);
+      if (dU) store_du_block(tiles[warp], u, e, B, rs, q, diag, stochastic, step, idx, planar ? nullptr : dU);
     }
     __syncwarp();
+    if (dU && planar) store_planar_block(tiles[warp], lane, q, dU);
     if (dU && dUH) store_dagger_block(tiles[warp], lane, B, rs, q, dUH);
     __syncwarp();
   }
@@ -955,12 +978,13 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) k_field_poly(PolyTerms V, int
 
 void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which, double2* U, float2* dU,
                        float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st,
-                       bool stochastic) {
+                       bool stochastic, bool planar) {
   RT_REQUIRE(deg >= 0 && deg < RT_MAX_POLY, RT_EINTERNAL, "field polynomial degree out of range");
   RT_REQUIRE(B <= 13, RT_EINTERNAL, "block size above 13");
+  RT_REQUIRE(!planar || B == 13, RT_EINTERNAL, "column-planar blocks are 13-function blocks");
   if (nnzb == 0) return;
   k_field_poly<<<(unsigned)poly_grid(nnzb), POLY_WARPS * 32, 0, st>>>(V, deg, s, which, U, dU, dUH, nnzb, rowidx, col,
-                                                                      B, rs32(B), stochastic ? 1 : 0);
+                                                                      B, rs32(B), stochastic ? 1 : 0, planar ? 1 : 0);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 

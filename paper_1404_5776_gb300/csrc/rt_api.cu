@@ -98,6 +98,7 @@ struct Sys {
   std::vector<double2*> Bp;       // coefficients of R(E) on P_K (Bp[0] includes -K_ref)
   float2 *dUr = nullptr, *dUHr = nullptr;  // U - I stochastically rounded to FP32, and its block dagger
   bool u64_stale = false;         // the FP64 U is not formed per step (field polynomial, reference split)
+  bool planar = false;            // dUr and Wf column-planar: the packed-FMA products of the reference split
   // maps
   int32_t *u_to_t = nullptr, *a_to_s = nullptr, *a_to_h = nullptr, *k_to_sT = nullptr, *k_to_hT = nullptr;
   int32_t *u_to_sinv = nullptr, *k_to_sinv = nullptr, *u_to_s = nullptr, *k_to_m = nullptr, *m_to_k = nullptr;
@@ -313,6 +314,8 @@ static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cpl
                "block product accumulator overlaps an operand");
   }
   int B = s.B;
+  RT_REQUIRE(!g.a_planar || (fp32 && cplx && B == 13 && !ti.tiles.built), RT_EINTERNAL,
+             "column-planar operands belong to the packed CUDA-core products");
   if (fp32 && cplx && B == 13 && !ad && !bd && ti.tiles.built && (epi == EPI_STORE || epi == EPI_DELTA_SANDWICH)) {
     g.tl_n = ti.tiles.n_tiles;
     g.tl_item0 = ti.tiles.item0;
@@ -590,6 +593,7 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
     if (s.B == 13) {  // the 13-function kernels read a pre-transposed dagger
       s.dUHr = c->arena.get_n<float2>(nvals32(s, s.pU));
       RT_CUDA_CHECK(cudaMemsetAsync(s.dUHr, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
+      s.planar = p.packed_fma != 0 && !p.tensor_cores;
     }
   }
   RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
@@ -1160,12 +1164,12 @@ static void reference_split_propagator(rt_ctx* c, Sys& s) {
     const double nU = (double)nvals(s, s.pU);
     run(c, PC_POLY, 0, 16.0 * nU * (deg + 1) + 16.0 * nU, [&] {  // read V_0..V_deg, write dU and dU^dagger
       launch_field_poly(V, deg, c->dstate, 0, nullptr, s.dUr, s.dUHr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B,
-                        c->ws, true);
+                        c->ws, true, s.planar);
     });
     s.u64_stale = true;
   } else {
     run(c, PC_MISC, 0, 0, [&] {
-      launch_round_u_sr(s.U, s.dUr, s.dUHr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->dstate, c->ws);
+      launch_round_u_sr(s.U, s.dUr, s.dUHr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B, c->dstate, c->ws, s.planar);
     });
   }
 }
@@ -1183,6 +1187,7 @@ static void sandwich_incremental(rt_ctx* c, Sys& s, int kick, int slot) {
     g.base = dK;  // W = dK + M from the same epilogue
     g.U = s.Wf;
     g.add_map = s.m_to_k;
+    g.a_planar = s.planar ? 1 : 0;  // dU in, W out column-planar
     gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, g, s.pM);
   } else {
     gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUr, s.Kf, s.Mf), s.pM);
@@ -1197,6 +1202,7 @@ static void sandwich_incremental(rt_ctx* c, Sys& s, int kick, int slot) {
   g.addend = s.Mf;
   g.add_map = s.k_to_m;
   g.base2 = s.Rm;
+  g.a_planar = s.planar ? 1 : 0;  // W column-planar
   gemm(c, s, PC_MUDAG, tK, true, true, false, !pre_t, EPI_DELTA_SANDWICH, g, s.pK);
 }
 
@@ -1446,6 +1452,7 @@ rt_status rt_default_params(rt_params* p) {
   p->hot_step_iters = 2;
   p->hot_fp64_iters = 1;
   p->tensor_cores = 0;
+  p->packed_fma = 0;
   p->precision = RT_FP64;
   p->full_step = 1;
   p->n_kick = 1;

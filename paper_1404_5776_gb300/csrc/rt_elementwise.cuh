@@ -50,9 +50,10 @@ void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const 
                    double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s,
                    const double* ref = nullptr, double* out = nullptr);
 // dU = U - I stochastically rounded to FP32 (draws keyed on s->step and the element) and its per-block
-// conjugate transpose dUH (if non-null), from an FP64 U
+// conjugate transpose dUH (if non-null), from an FP64 U; with `planar` (13-function blocks) dU is written
+// column-planar (per column: real parts of rows 0..15, then imaginary parts), dUH in the row layout
 void launch_round_u_sr(const double2* U, float2* dU, float2* dUH, int64_t nnzb, const int32_t* rowidx,
-                       const int32_t* col, int B, const DevState* s, cudaStream_t st);
+                       const int32_t* col, int B, const DevState* s, cudaStream_t st, bool planar = false);
 void launch_zaxpy(double2* z, const double2* x, const double2* y, double a, int64_t n, cudaStream_t st);
 void launch_axpy32(float2* z, const float2* x, const float2* y, float a, int64_t n, cudaStream_t st);
 void launch_m4_omega32(const double* T1, const double* T2, const int32_t* u_to_t, const float* C21, const float* C12,
@@ -67,10 +68,11 @@ struct PolyTerms {
 };
 // U = sum_{m<=deg} E^m V_m at E = s->E[which] (Horner, FP64); writes U (FP64, if non-null) and/or
 // dU = U - I with its per-block conjugate transpose dUH in FP32 (padded rows), if non-null, rounded to
-// nearest or, with `stochastic`, stochastically (draws keyed on s->step and the element)
+// nearest or, with `stochastic`, stochastically (draws keyed on s->step and the element); with `planar`
+// (13-function blocks) dU is written column-planar as in launch_round_u_sr
 void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which, double2* U, float2* dU,
                        float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st,
-                       bool stochastic = false);
+                       bool stochastic = false, bool planar = false);
 // R = sum_{p<=deg} E^p C_p at E = s->E[which] (Horner, FP64) on the upper blocks of a pattern
 void launch_poly_upper(const PolyTerms& C, int deg, const DevState* s, int which, double2* R, int64_t nnzb,
                        const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st);

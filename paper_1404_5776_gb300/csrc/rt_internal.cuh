@@ -180,6 +180,8 @@ struct GemmArgs {
   int* err;                 // device error word: the largest code of a bounded wait that gave up
                             // (1: wait expired, copies drained; 2: the drain expired too)
   long long wait_ns;        // budget of one bounded wait (FP32 kernels), nanoseconds
+  int a_planar;             // complex 13-function FP32: A (and the W written by the delta
+                            // form) column-planar, the packed-FMA kernel
   // row tiles (tensor-core products)
   int64_t tl_n;
   const int32_t* tl_item0;

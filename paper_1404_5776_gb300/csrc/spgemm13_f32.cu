@@ -64,6 +64,39 @@ __device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 c) {
   return c;
 }
 
+// Two FP32 values in one 64-bit register (low half first) and the packed
+// arithmetic of sm_100+ on such pairs: one instruction, two roundings.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(uint64_t v) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+  return f;
+}
+__device__ __forceinline__ uint64_t fma_x2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul_x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t add_x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub_x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 __device__ __forceinline__ void amax_nonneg(unsigned long long* p, double v) {
   atomicMax(p, (unsigned long long)__double_as_longlong(v));
 }
@@ -179,7 +212,18 @@ __device__ __forceinline__ int stream_triples(V* wsm, uint64_t* bar, const V* __
 // dropped).  Partial sums meet in shared memory; the epilogue then walks the
 // 169 elements of the block with all 32 lanes.
 // ---------------------------------------------------------------------------
-template <int EPI>
+//
+// PK = true: the packed variant.  A arrives column-planar (for each column m
+// of the block: the real parts of rows 0..15, then the imaginary parts; rows
+// 13..15 zero), so a column of A is a run of broadcast loads, and a lane
+// (h, c) accumulates row pairs (2p, 2p+1) of its output column with one
+// fma.rn.f32x2 per pair and partial product: per column m of A,
+//   re += A_re(:,m) B_re(m,c),  re_n += A_im(:,m) B_im(m,c),
+//   im += A_re(:,m) B_im(m,c) + A_im(:,m) B_re(m,c),
+// and the running sum takes re - re_n and im once per triple.  B stays in
+// the row layout; W (delta form) is written column-planar, since it is the A
+// operand of the next product.
+template <int EPI, bool PK>
 __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
   constexpr int NT = 2;
   constexpr int WBUF = NT * Slot<float2>::STRIDE;  // one stage of one warp (float2)
@@ -202,8 +246,68 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
   float2 acc[BS];
 #pragma unroll
   for (int r = 0; r < BS; ++r) acc[r] = make_float2(0.f, 0.f);
+  constexpr int NP = (BS + 1) / 2;  // row pairs (the last one holds padding row 13)
+  uint64_t top_re[NP], top_im[NP];  // packed variant: running sums of row pairs
+#pragma unroll
+  for (int p = 0; p < NP; ++p) top_re[p] = top_im[p] = 0ull;
 
-  const int ok = stream_triples<float2, NT, C_STAGES>(
+  int ok;
+  if constexpr (PK) {
+    ok = stream_triples<float2, NT, C_STAGES>(
+        wsm, bar, static_cast<const float2*>(g.A), static_cast<const float2*>(g.B),
+        static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns,
+        [&](const float2* sA, const float2* sB) {
+          const float* a = reinterpret_cast<const float*>(sA);
+          uint64_t pre[NP], pren[NP], pim[NP];  // this triple's partial sums
+#pragma unroll
+          for (int m = 0; m < BS; ++m) {
+            const float2 b = sB[m * RS + c];
+            const uint64_t bxx = pk2(b.x, b.x), byy = pk2(b.y, b.y);
+            const float* colm = a + m * 2 * RS;  // real parts of column m, then imaginary parts
+            uint64_t ar[NP], ai[NP];
+#pragma unroll
+            for (int q4 = 0; q4 < 3; ++q4) {
+              const float4 r4 = reinterpret_cast<const float4*>(colm)[q4];
+              const float4 i4 = reinterpret_cast<const float4*>(colm + RS)[q4];
+              ar[2 * q4] = pk2(r4.x, r4.y);
+              ar[2 * q4 + 1] = pk2(r4.z, r4.w);
+              ai[2 * q4] = pk2(i4.x, i4.y);
+              ai[2 * q4 + 1] = pk2(i4.z, i4.w);
+            }
+            {
+              const float2 r2 = reinterpret_cast<const float2*>(colm)[6];  // rows 12, 13
+              const float2 i2 = reinterpret_cast<const float2*>(colm + RS)[6];
+              ar[6] = pk2(r2.x, r2.y);
+              ai[6] = pk2(i2.x, i2.y);
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+              if (m == 0) {
+                pre[p] = mul_x2(ar[p], bxx);
+                pren[p] = mul_x2(ai[p], byy);
+                pim[p] = fma_x2(ai[p], bxx, mul_x2(ar[p], byy));
+              } else {
+                pre[p] = fma_x2(ar[p], bxx, pre[p]);
+                pren[p] = fma_x2(ai[p], byy, pren[p]);
+                pim[p] = fma_x2(ar[p], byy, pim[p]);
+                pim[p] = fma_x2(ai[p], bxx, pim[p]);
+              }
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            top_re[p] = add_x2(top_re[p], sub_x2(pre[p], pren[p]));
+            top_im[p] = add_x2(top_im[p], pim[p]);
+          }
+        });
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float2 re = upk2(top_re[p]), im = upk2(top_im[p]);
+      acc[2 * p] = make_float2(re.x, im.x);
+      if (2 * p + 1 < BS) acc[2 * p + 1] = make_float2(re.y, im.y);
+    }
+  } else {
+  ok = stream_triples<float2, NT, C_STAGES>(
       wsm, bar, static_cast<const float2*>(g.A), static_cast<const float2*>(g.B),
       static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns,
       [&](const float2* sA, const float2* sB) {
@@ -213,16 +317,21 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
 #pragma unroll
         for (int r = 0; r < BS; ++r) {
           const float4* row = reinterpret_cast<const float4*>(sA + r * RS);
-          float2 v = acc[r];
+          // two-level sum: this triple's 13 terms in a fresh register, then
+          // one addition into the running sum (the running sum takes one
+          // rounding per triple instead of one per term)
+          float2 v = make_float2(0.f, 0.f);
 #pragma unroll
           for (int m2 = 0; m2 < 7; ++m2) {
             const float4 a2 = row[m2];  // A[r][2m2], A[r][2m2+1] (broadcast in the group)
             v = cfma2(make_float2(a2.x, a2.y), bcol[2 * m2], v);
             if (2 * m2 + 1 < BS) v = cfma2(make_float2(a2.z, a2.w), bcol[2 * m2 + 1], v);
           }
-          acc[r] = v;
+          acc[r].x += v.x;
+          acc[r].y += v.y;
         }
       });
+  }
   if (ok != WAIT_OK) {
     if (lane == 0 && g.err) atomicMax(g.err, ok);
     return;
@@ -279,12 +388,33 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
         kv[k] = make_double2(0.0, 0.0);
         if (e < NE && kq >= 0) kv[k] = Kb[(int64_t)kq * NE + e];
       }
+      if constexpr (PK) {
+        // column-planar W through shared memory (after the partial sums)
+        float2* wt = part + NT * SB;
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const int e = lane + 32 * k;
-        if (e < NE)
-          W[(int64_t)q * SB + (e / BS) * RS + e % BS] =
-              make_float2((float)((double)sum[k].x + kv[k].x), (float)((double)sum[k].y + kv[k].y));
+        for (int k = 0; k < EPT; ++k) {
+          const int e = lane + 32 * k;
+          if (e < NE) wt[e] = make_float2((float)((double)sum[k].x + kv[k].x), (float)((double)sum[k].y + kv[k].y));
+        }
+        __syncwarp();
+        float* __restrict__ Wp = reinterpret_cast<float*>(W) + (int64_t)q * (2 * SB);
+        for (int idx = lane; idx < 2 * SB; idx += 32) {
+          const int m = idx / (2 * RS), w = idx % (2 * RS), r = w % RS;
+          float v = 0.f;
+          if (r < BS) {
+            const float2 t = wt[r * BS + m];
+            v = w >= RS ? t.y : t.x;
+          }
+          Wp[idx] = v;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int e = lane + 32 * k;
+          if (e < NE)
+            W[(int64_t)q * SB + (e / BS) * RS + e % BS] =
+                make_float2((float)((double)sum[k].x + kv[k].x), (float)((double)sum[k].y + kv[k].y));
+        }
       }
     }
   } else if constexpr (EPI == EPI_DELTA_SANDWICH) {
@@ -496,6 +626,8 @@ __global__ void __launch_bounds__(R_WARPS * 32, MINB_R) k_gemm13_r32(GemmArgs g)
 // theirs.  B^dagger operands must be passed pre-transposed (b_dag = false).
 bool launch_gemm13_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const GemmArgs& g, cudaStream_t st) {
   using namespace f32;
+  RT_REQUIRE(!g.a_planar || (cplx && !a_dag && !b_dag), RT_EINTERNAL,
+             "column-planar A only for complex products with untransposed operands");
   if (a_dag || b_dag) return false;
   if (g.n_items == 0) return true;
   RT_REQUIRE(g.zero != nullptr, RT_EINTERNAL, "FP32 products need a zero block");
@@ -505,17 +637,23 @@ bool launch_gemm13_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const Ge
   const size_t smem_c = SMEM_C, smem_r = SMEM_R;
   static bool attr_done = false;
   if (!attr_done) {
-    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_DELTA_SANDWICH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_STORE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_DELTA_SANDWICH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_ADD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_STORE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_DELTA_SANDWICH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_r32<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_r32<EPI_STORE_ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
     attr_done = true;
   }
-  if (cplx) {
-    if (epi == EPI_STORE) k_gemm13_c32<EPI_STORE><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
-    else if (epi == EPI_ADD) k_gemm13_c32<EPI_ADD><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
-    else if (epi == EPI_DELTA_SANDWICH) k_gemm13_c32<EPI_DELTA_SANDWICH><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+  if (cplx && g.a_planar) {
+    if (epi == EPI_STORE) k_gemm13_c32<EPI_STORE, true><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+    else if (epi == EPI_DELTA_SANDWICH) k_gemm13_c32<EPI_DELTA_SANDWICH, true><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+    else RT_REQUIRE(false, RT_EINTERNAL, "column-planar A only with the store and delta-sandwich epilogues");
+  } else if (cplx) {
+    if (epi == EPI_STORE) k_gemm13_c32<EPI_STORE, false><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+    else if (epi == EPI_ADD) k_gemm13_c32<EPI_ADD, false><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+    else if (epi == EPI_DELTA_SANDWICH) k_gemm13_c32<EPI_DELTA_SANDWICH, false><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
     else return false;
   } else {
     if (epi == EPI_STORE) k_gemm13_r32<EPI_STORE><<<(unsigned)grid_r, R_WARPS * 32, smem_r, st>>>(g);

@@ -286,8 +286,24 @@ def dense_to_blocks(bsize, rowptr, col, dense):
 # geometry
 # ----------------------------------------------------------------------------
 
-def diamond_positions(ncell: int, a: float = A_DIAMOND, jitter: float = 0.05, seed: int = 0):
-    """ncell^3 conventional diamond cells (8 atoms each), seeded jitter, wrapped."""
+def _morton_sort(pos: np.ndarray, L: float, bits: int = 10) -> np.ndarray:
+    """Atoms reordered along a Morton (Z-order) curve over the periodic cube of
+    side L: coordinates quantised to 2^bits steps, bits interleaved x, y, z."""
+    q = np.clip((pos / L * (1 << bits)).astype(np.int64), 0, (1 << bits) - 1)
+    code = np.zeros(len(pos), dtype=np.int64)
+    for b in range(bits):
+        for d in range(3):
+            code |= ((q[:, d] >> b) & 1) << (3 * b + d)
+    return pos[np.argsort(code, kind="stable")]
+
+
+def diamond_positions(ncell: int, a: float = A_DIAMOND, jitter: float = 0.05, seed: int = 0,
+                      order: str = "lattice"):
+    """ncell^3 conventional diamond cells (8 atoms each), seeded jitter, wrapped.
+
+    order "lattice": cell by cell (z fastest), the 8 basis atoms of a cell in
+    turn; "morton": the same atoms sorted along a Morton curve (spatially
+    compact runs of atoms, as a linear-scaling code orders its partitions)."""
     basis = np.array([
         [0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0],
         [.25, .25, .25], [.25, .75, .75], [.75, .25, .75], [.75, .75, .25],
@@ -301,6 +317,10 @@ def diamond_positions(ncell: int, a: float = A_DIAMOND, jitter: float = 0.05, se
     L = ncell * a
     pos = np.mod(pos, L)
     pos[pos >= L] -= L
+    if order == "morton":
+        pos = _morton_sort(pos, L)
+    elif order != "lattice":
+        raise ValueError(f"unknown atom order {order!r}")
     return pos, np.array([L, L, L], dtype=np.float64)
 
 
@@ -586,8 +606,8 @@ def build_system(pos, cell, species: Sequence[str], r_S: float, r_H: float,
 
 
 def diamond_system(ncell: int, basis: str = "sp4", r_S: float = 6.0, r_H: float = 6.0,
-                   jitter: float = 0.05, seed: int = 0, noise_seed: int = 1) -> System:
-    pos, cell = diamond_positions(ncell, jitter=jitter, seed=seed)
+                   jitter: float = 0.05, seed: int = 0, noise_seed: int = 1, order: str = "lattice") -> System:
+    pos, cell = diamond_positions(ncell, jitter=jitter, seed=seed, order=order)
     return build_system(pos, cell, [basis] * len(pos), r_S, r_H, noise_seed=noise_seed)
 
 
