@@ -69,8 +69,11 @@ def parse():
                     help="run only the mixed-precision context (FOE ground state, kick, warm-up, steps) and print "
                          "its per-kernel-class times: a small resident set for kernel captures, no benchmark line")
     ap.add_argument("--literal", action="store_true", help="--kernel-case: the literal FP32 path")
-    ap.add_argument("--packed-fma", action="store_true",
-                    help="reference split: the complex products with packed two-lane FMAs (column-planar U - I and W)")
+    ap.add_argument("--only-split", action="store_true",
+                    help="time only the FP64 step and the reference-split mixed step (less device memory, e.g. "
+                         "for larger radii)")
+    ap.add_argument("--scalar-fma", action="store_true",
+                    help="reference split: the row-layout complex products with scalar FMAs instead of packed ones")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="FP32 contexts run the sandwich's 13-function products on the tensor cores (tcgen05)")
     ap.add_argument("--study", default=None, choices=["truncation", "scaling", "batching", "propagators",
@@ -172,8 +175,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu capture of
 # the same kernel and workload, keyed by (path, kernel class); None when the kernel
 # changed after the capture.
-TRAFFIC = {("diamond 4096 atoms x 13 functions, r_S=r_H=7A, r_Sinv=r_T=r_U=r_K=r_M=10A, dt=0.05, EM 6 terms, "
-            "x-kick 1e-3", "fp32", "gemm_M=UK"): 24.577e9 + 2.605e9}  # k_gemm13_c32<EPI_STORE>
+TRAFFIC = {}
 
 
 def derived_alu_peaks(torch, sm_max_mhz):
@@ -285,7 +287,7 @@ def run_gpu(args):
     R = args.radius
     radii = dict(r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R)
     common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=8192, tensor_cores=1 if args.tensor_cores else 0,
-                  packed_fma=1 if args.packed_fma else 0, **radii)
+                  packed_fma=0 if args.scalar_fma else 1, **radii)
     split_ok = args.prop == "em" and args.basis in ("spd13", "sp4")
 
     # --- FP64 context (the plain FP64 GPU path): ground state (untimed set-up), kick
@@ -301,6 +303,7 @@ def run_gpu(args):
     # One-time set-up, host wall clock: rt_create, rt_inverse (Hotelling S^-1
     # and the V_m), and the reference (K_ref, the B_p) formed by the first step.
     setup_s = {}
+    launch_shapes, launch_shape_ms = None, None
     c32s = None
     if split_ok:
         torch.cuda.synchronize()
@@ -321,23 +324,37 @@ def run_gpu(args):
                            "polynomial V_m of U: FP64 block products); the first rt_step (K_ref and the "
                            "coefficients B_p of R(E): 2 (taylor_terms)^2 + taylor_terms FP64 complex products, "
                            "then one step)"}
+        # launch shapes of the two products (stages per warp, one-shot or
+        # persistent grid): timed on this context's own products, fastest kept
+        if not args.tensor_cores:
+            t4 = time.perf_counter()
+            tuned = c32s.autotune(reps=2)
+            setup_s["autotune"] = round(time.perf_counter() - t4, 3)
+            launch_shapes = {c32s.STAGES[st]: {"stages_per_warp": v[0], "persistent": v[1]}
+                             for st, v in tuned["chosen"].items()}
+            launch_shape_ms = {f"{r['what']}: stages {r['stages_per_warp']}, persistent {r['persistent']}":
+                               round(r["ms"], 3) for r in tuned["rows"]}
     # the literal mixed path (FP32 block products on the whole K): faster set-up,
     # but its dipole error grows with the step count (reported, not the headline)
-    c32l = rtm.RT(s, precision="fp32", **common)
-    c32l.inverse()
-    c32l.set_density(0, 0, K1)
-    # propagation step (the delta kick leaves H constant: U built once, FP64):
-    # FP64 and the reference split
-    c64p = rtm.RT(s, precision="fp64", full_step=0, **common)
-    c64p.inverse()
-    c64p.set_density(0, 0, K1)
-    c64p.propagator(0.0)
-    c32p = None
-    if args.basis in ("spd13", "sp4"):
+    c32l = c64p = c32p = None
+    if not args.only_split:
+        c32l = rtm.RT(s, precision="fp32", **common)
+        c32l.inverse()
+        c32l.set_density(0, 0, K1)
+        # propagation step (the delta kick leaves H constant: U built once, FP64):
+        # FP64 and the reference split
+        c64p = rtm.RT(s, precision="fp64", full_step=0, **common)
+        c64p.inverse()
+        c64p.set_density(0, 0, K1)
+        c64p.propagator(0.0)
+    if args.basis in ("spd13", "sp4") and not args.only_split:
         c32p = rtm.RT(s, precision="fp32", full_step=0, incremental=1, **common)
         c32p.inverse()
         c32p.set_density(0, 0, K1)
         c32p.propagator(0.0)
+        if c32s is not None and launch_shapes is not None:  # same products: the headline's tuned shapes
+            for st, v in tuned["chosen"].items():
+                c32p.set_launch_shape(st, v[0], v[1])
 
     n64 = args.fp64_steps if args.fp64_steps is not None else args.steps
 
@@ -364,22 +381,23 @@ def run_gpu(args):
     clocks.start()
     ms64 = timed(c64, n64, args.warmup, "fp64")
     ms32s = timed(c32s, args.steps, args.warmup, "fp32_split") if c32s else float("nan")
-    ms32l = timed(c32l, args.steps, args.warmup, "fp32_literal")
-    ms64p = timed(c64p, n64, args.warmup, "fp64_propagation")
+    ms32l = timed(c32l, args.steps, args.warmup, "fp32_literal") if c32l else float("nan")
+    ms64p = timed(c64p, n64, args.warmup, "fp64_propagation") if c64p else float("nan")
     ms32p = timed(c32p, args.steps, args.warmup, "fp32_split_propagation") if c32p else float("nan")
     clk = clocks.stop()
     # the FP64 reference run continues to --gate-steps for the dipole comparison
     extra = args.gate_steps - (args.warmup + n64)
     if extra > 0:
         c64.step(extra)
-        c64p.step(extra)
+        if c64p:
+            c64p.step(extra)
 
     flops64, _ = c64.step_work()
-    flops32l, _ = c32l.step_work()
+    flops32l, _ = c32l.step_work() if c32l else (float("nan"), 0.0)
     flops32s, _ = c32s.step_work() if c32s else (float("nan"), 0.0)
-    o64, o64p = c64.observables(0, 0), c64p.observables(0, 0)
+    o64, o64p = c64.observables(0, 0), (c64p.observables(0, 0) if c64p else None)
     gate_s = _dipole_errors(c32s.observables(0, 0), o64) if c32s else None
-    gate_l = _dipole_errors(c32l.observables(0, 0), o64)
+    gate_l = _dipole_errors(c32l.observables(0, 0), o64) if c32l else None
     gate_p = _dipole_errors(c32p.observables(0, 0), o64p) if c32p else None
     BAR = 1e-6
     headline_ok = bool(gate_s and gate_s["induced"] is not None and gate_s["induced"] <= BAR)
@@ -481,17 +499,20 @@ def run_gpu(args):
                               "step_tflop": round(flops32l / 1e12, 4), "timed_steps": args.steps,
                               "dipole_err": gate_l,
                               "what": ("T = T0 - E T_D, Taylor powers and the delta-form sandwich as FP32 block "
-                                       "products on the whole K; its error grows with the step count")},
+                                       "products on the whole K; its error grows with the step count")}
+            if c32l else None,
             "speedup_split_vs_fp64": round(ms64 / ms32s, 2) if c32s else None,
-            "speedup_literal_vs_fp64": round(ms64 / ms32l, 2),
+            "speedup_literal_vs_fp64": round(ms64 / ms32l, 2) if c32l else None,
             "propagation_step": {
                 "what": "delta kick: H is constant for t > 0, U built once (FP64) and reused; sandwich + traces",
                 "fp64": {"ms_per_step": round(ms64p, 3), "steps_per_s": round(1e3 / ms64p, 4)},
                 "mixed_reference_split": {"ms_per_step": round(ms32p, 3), "steps_per_s": round(1e3 / ms32p, 4),
                                           "dipole_err": gate_p} if c32p else None,
-                "speedup": round(ms64p / ms32p, 2) if c32p else None},
+                "speedup": round(ms64p / ms32p, 2) if c32p else None} if c64p else None,
             "hotelling": {"iters": it64, "residual": res64},
             "setup_s": setup_s,
+            "launch_shapes": launch_shapes,
+            "launch_shape_ms": launch_shape_ms,
         },
         "roofline": roof,
         "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
@@ -612,7 +633,7 @@ def precision_study(args):
     R = args.radius
     n = args.precision_study
     common = dict(dt=0.05, prop=args.prop, n_kick=1, obs_capacity=n + 8, r_Sinv=R, r_T=R, r_U=R, r_K=R, r_M=R,
-                  tensor_cores=1 if args.tensor_cores else 0, packed_fma=1 if args.packed_fma else 0)
+                  tensor_cores=1 if args.tensor_cores else 0, packed_fma=0 if args.scalar_fma else 1)
     c64 = rtm.RT(s, precision="fp64", **common)
     c64.inverse()
     c64.ground_state(0, args.foe_order, mu, 0.01, e_lo, e_hi)
@@ -800,7 +821,7 @@ def kernel_case(args):
     s = workload(args)
     mu, e_lo, e_hi = model_spectrum(args)
     R = args.radius
-    kw = dict(precision="fp32", tensor_cores=1 if args.tensor_cores else 0, packed_fma=1 if args.packed_fma else 0)
+    kw = dict(precision="fp32", tensor_cores=1 if args.tensor_cores else 0, packed_fma=0 if args.scalar_fma else 1)
     if not args.literal and args.prop == "em":
         kw.update(incremental=1, field_poly=1)
     ctx = rtm.RT(s, dt=0.05, prop=args.prop, obs_capacity=args.steps + args.warmup + 8,
@@ -828,15 +849,16 @@ def batching_study(args):
     x, y and z kicks, advanced together (one graph per step): diamond cells of
     512 ... 8000 atoms (13 functions for 512, 1728, 4096, 8000; 4 for 1000,
     2744, 5832) and the H-terminated Si cluster (4 and 1 functions), r = 8 A.
-    Mixed precision timed over K steps; FP64 over a few steps for the dipole
-    agreement."""
+    Mixed precision (reference split) timed over K steps; the FP64 run over the
+    same steps for the dipole agreement.  The two contexts run one after the
+    other (together they would not fit in device memory)."""
     import torch
 
     import synth
 
     import paper_1404_5776_gb300 as rtm
     rtm.build()
-    R = args.radius
+    R = 8.0  # the batching workload's radius
     spec = [(4, "spd13"), (5, "sp4"), (6, "spd13"), (7, "sp4"), (8, "spd13"), (9, "sp4"), (10, "spd13")]
     t0 = time.perf_counter()
     systems = [synth.diamond_system(nc, b, 7.0, 7.0) for nc, b in spec]
@@ -862,13 +884,29 @@ def batching_study(args):
         for k in range(3):
             c64.kick(si, k, k, 1e-3)
     K1 = {(si, k): c64.matrix(si, rtm.RT_MAT_K, k) for si in range(len(systems)) for k in range(3)}
-    # mixed context from the same K(0+)
-    c32 = rtm.RT(systems, precision="fp32", **common)
+    # the FP64 run over every step the mixed run takes, then its context is freed
+    n64 = 1 + args.warmup + args.steps
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    c64.step(n64)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / n64
+    o64s = {(si, k): c64.observables(si, k) for si in range(len(systems)) for k in range(3)}
+    mem64 = torch.cuda.max_memory_allocated() / 1e9
+    c64.close()
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    # mixed context (reference split, EM field polynomial) from the same K(0+);
+    # its grouped products (one launch per product and block size) tuned
+    c32 = rtm.RT(systems, precision="fp32", incremental=1, field_poly=1, **common)
     c32.inverse()
     for (si, k), Kv in K1.items():
         c32.set_density(si, k, Kv)
     del K1
-    mem = torch.cuda.max_memory_allocated() / 1e9
+    c32.step(1)  # the reference (K_ref, the B_p of every system)
+    tuned = c32.autotune(reps=2)
     c32.step(args.warmup)
     c32.synchronize()
     torch.cuda.synchronize()
@@ -882,17 +920,11 @@ def batching_study(args):
     ms32 = e0.elapsed_time(e1) / args.steps
     launches = c32.step_kernels()
     flops, _ = c32.step_work()
-    n64 = 3
-    torch.cuda.synchronize()
-    e0.record()
-    c64.step(n64)
-    e1.record()
-    torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1) / n64
+    mem32 = torch.cuda.max_memory_allocated() / 1e9
     runs = []
     for si, (nc, b) in enumerate(spec + [(None, "si_h")]):
         for k in range(3):
-            o64 = c64.observables(si, k)
+            o64 = o64s[(si, k)]
             o32 = c32.observables(si, k)[:len(o64)]
             p64, p32 = o64[:, 3 + 2 * k], o32[:, 3 + 2 * k]
             ind = np.abs(p64 - p64[0]).max()
@@ -900,15 +932,19 @@ def batching_study(args):
                          "dipole_err_rel_P": float(np.abs(p32 - p64).max() / np.abs(p64).max()),
                          "dipole_err_rel_induced": float(np.abs(p32 - p64).max() / ind) if ind > 0 else None})
     c32.close()
-    c64.close()
     n_atoms = sum(int(x.n_atoms) for x in systems)
     out = {"study": "batching", "systems": [{"atoms": int(x.n_atoms), "functions": int(x.n)} for x in systems],
            "total_atoms": n_atoms, "kicks": 3, "radius_A": R, "steps": args.steps, "warmup": args.warmup,
            "cluster_gap_Ha": gap_c, "host_build_s": round(t_build, 1),
-           "mixed": {"ms_per_step": round(ms32, 3), "batch_steps_per_s": round(1e3 / ms32, 3),
+           "mixed": {"path": "reference split, EM field polynomial; one launch per product and block size",
+                     "ms_per_step": round(ms32, 3), "batch_steps_per_s": round(1e3 / ms32, 3),
                      "atom_kick_steps_per_s": round(3 * n_atoms * 1e3 / ms32, 1),
-                     "algorithmic_tflops": round(flops / ms32 / 1e9, 2), "kernels_per_step": int(launches)},
-           "device_gb_both_contexts": round(mem, 2),
+                     "algorithmic_tflops": round(flops / ms32 / 1e9, 2), "kernels_per_step": int(launches),
+                     "launch_shapes": {c32.STAGES[st]: {"stages_per_warp": v[0], "persistent": v[1]}
+                                       for st, v in tuned["chosen"].items()},
+                     "tuning_ms": [{k: r[k] for k in ("what", "stages_per_warp", "persistent", "ms")}
+                                   for r in tuned["rows"]]},
+           "device_gb": {"fp64_context": round(mem64, 2), "mixed_context": round(mem32, 2)},
            "fp64": {"ms_per_step": round(ms64, 1), "timed_steps": n64},
            "speedup_mixed_vs_fp64": round(ms64 / ms32, 2),
            "dipole_agreement_over_fp64_steps": runs}

@@ -199,12 +199,12 @@ typedef struct {
                                FP32 and its error adds up coherently over long
                                runs; 0 (default): FP32 CUDA cores              */
   int32_t packed_fma;       /* reference split (incremental = 1) on the CUDA
-                               cores with 13-function blocks: 1 keeps U - I and
-                               W = dK + M column-planar and runs the complex
-                               products with packed two-lane FMAs
-                               (fma.rn.f32x2, rows in pairs); 0 (default): the
-                               row-layout kernel with scalar FMAs.  Same sums,
-                               in a different order                            */
+                               cores with 13-function blocks: 1 (default) keeps
+                               U - I and W = dK + M column-planar and runs the
+                               complex products with packed two-lane FMAs
+                               (fma.rn.f32x2, rows in pairs; measured 8 %
+                               faster); 0: the row-layout kernel with scalar
+                               FMAs.  Same sums, in a different order          */
 } rt_params;
 
 typedef struct {
@@ -266,8 +266,35 @@ RT_API rt_status rt_kick(rt_ctx* ctx, int32_t sys, int32_t kick, int32_t dir, do
 RT_API rt_status rt_propagator(rt_ctx* ctx, double t);
 
 /* n time steps K <- U K U^dagger for every (system, kick), each followed by the
- * observables.  With full_step, U is rebuilt at each step's midpoint. */
+ * observables.  With full_step, U is rebuilt at each step's midpoint.
+ * In the reference split on the CUDA cores (incremental = 1, tensor_cores = 0)
+ * the two block products of the step (M and K', Sec. II.A) run as one launch
+ * per product and block size over every (system, kick) pair, the pairs with
+ * the most block triples first. */
 RT_API rt_status rt_step(rt_ctx* ctx, int32_t n);
+
+/* Launch-shape tuner of the grouped products of the reference split (no
+ * counterpart in the paper: a property of the GPU kernels).  Stages: 0 = M of
+ * the 13-function systems, 1 = their K', 2 = M of the 4-function systems,
+ * 3 = their K'.  For every stage present it times each candidate shape -
+ * stages per warp of the 13-function kernel (2 or 3) and a one-shot grid or a
+ * persistent one (one resident wave of CTAs walking the items) - on the
+ * context's own products: one warm-up launch, then `reps` (1..100) launches
+ * between CUDA events, and keeps the fastest.  The densities are not changed
+ * (the K' launches write into scratch copies of their outputs; the M
+ * launches write only M and W, which every step forms again).  Allocates the
+ * scratch through the context's allocator and synchronises.  rows: host
+ * [max_rows][4] of (stage, stages per warp, persistent, chosen 0/1) and ms:
+ * host [max_rows], milliseconds per launch; n_rows: rows produced (may exceed
+ * max_rows; may be NULL).  RT_ESTATE when the context has no such products. */
+RT_API rt_status rt_autotune(rt_ctx* ctx, int32_t reps, int32_t max_rows, int32_t* n_rows, int32_t* rows,
+                             double* ms);
+
+/* Sets (or reads) the launch shape of one stage (as in rt_autotune), e.g. a
+ * shape a caller cached from an earlier tuning run: stages per warp 2 or 3
+ * (3 only for stages 0 and 1), persistent 0 or 1.  Default: 2, 0. */
+RT_API rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t stage, int32_t stages, int32_t persistent);
+RT_API rt_status rt_get_launch_shape(rt_ctx* ctx, int32_t stage, int32_t* stages, int32_t* persistent);
 
 /* Copies the observables recorded since the previous call for (sys, kick) to
  * host `out` [max_steps][RT_NOBS] in step order; *n_out = steps copied.

@@ -12,6 +12,7 @@ are exported as thin wrappers; the class RT bundles them for one context.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 from typing import Optional, Sequence
 
@@ -40,7 +41,8 @@ EXPORTED = ["rt_default_params", "rt_create", "rt_set_field", "rt_inverse", "rt_
             "rt_kick", "rt_propagator", "rt_step", "rt_observables", "rt_pattern_size", "rt_get_pattern",
             "rt_matrix_size", "rt_get_matrix", "rt_unitarity", "rt_step_work", "rt_step_kernels", "rt_profile", "rt_profile_read",
             "rt_get_state", "rt_set_state", "rt_synchronize", "rt_last_error", "rt_destroy", "rt_traces_noalloc",
-            "rt_debug_inject", "rt_check_triples", "rt_debug_check"]
+            "rt_debug_inject", "rt_check_triples", "rt_debug_check", "rt_autotune", "rt_set_launch_shape",
+            "rt_get_launch_shape"]
 
 
 class rt_system(ctypes.Structure):
@@ -116,6 +118,9 @@ def load(path: Optional[str] = None):
         "rt_check_triples": [I32, P, P, I32, P, P, I32, P, P, I32, I64, P, P, P, I64, P],
         "rt_debug_check": [P, P],
         "rt_traces_noalloc": [P, I64, P, P, P, I32, P, P, P, P, P, P, I32, P, P],
+        "rt_autotune": [P, I32, I32, P, P, P],
+        "rt_set_launch_shape": [P, I32, I32, I32],
+        "rt_get_launch_shape": [P, I32, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -391,6 +396,63 @@ class RT:
 
     def synchronize(self):
         self._c(self.lib.rt_synchronize(self.ctx))
+
+    # -- launch shapes of the grouped products (reference split, CUDA cores)
+    STAGES = {0: "M, 13 functions", 1: "K', 13 functions", 2: "M, 4 functions", 3: "K', 4 functions"}
+
+    def set_launch_shape(self, stage: int, stages: int, persistent: int):
+        self._c(self.lib.rt_set_launch_shape(self.ctx, stage, stages, persistent))
+
+    def get_launch_shape(self, stage: int):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        self._c(self.lib.rt_get_launch_shape(self.ctx, stage, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def _tune_key(self):
+        try:
+            import torch
+            dev = torch.cuda.get_device_name()
+        except Exception:  # the key only names the device
+            dev = "cuda"
+        sysk = [(int(s.n_atoms), int(np.sum(s.bsize)), int(np.max(s.bsize))) for s in self.systems]
+        pk = self.params
+        return json.dumps([dev, sysk, pk.n_kick, pk.r_U, pk.r_K, pk.r_M, pk.packed_fma, pk.precision])
+
+    def autotune(self, reps: int = 3, cache: Optional[str] = None):
+        """Picks the launch shape of every grouped product stage (rt_autotune)
+        and returns {"source", "rows", "chosen"}.  With `cache` (a JSON file
+        path), a shape tuned earlier for the same device, systems and
+        parameters is applied without timing, and a new one is stored."""
+        key = self._tune_key()
+        store = {}
+        if cache and os.path.exists(cache):
+            try:
+                with open(cache) as f:
+                    store = json.load(f)
+            except (OSError, ValueError):
+                store = {}
+        if key in store:
+            for st, (ns, pers) in store[key].items():
+                self.set_launch_shape(int(st), int(ns), int(pers))
+            return {"source": "cache", "rows": [], "chosen": {int(k): tuple(v) for k, v in store[key].items()}}
+        mx = 64
+        n = ctypes.c_int32()
+        rows = np.zeros((mx, 4), dtype=np.int32)
+        ms = np.zeros(mx)
+        self._c(self.lib.rt_autotune(self.ctx, reps, mx, ctypes.byref(n), _p(rows), _p(ms)))
+        out_rows = [{"stage": int(r[0]), "what": self.STAGES[int(r[0])], "stages_per_warp": int(r[1]),
+                     "persistent": int(r[2]), "chosen": bool(r[3]), "ms": float(t)}
+                    for r, t in zip(rows[:min(n.value, mx)], ms[:min(n.value, mx)])]
+        chosen = {r["stage"]: (r["stages_per_warp"], r["persistent"]) for r in out_rows if r["chosen"]}
+        if cache:
+            store[key] = {str(k): list(v) for k, v in chosen.items()}
+            d = os.path.dirname(os.path.abspath(cache))
+            os.makedirs(d, exist_ok=True)
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(store, f, indent=1)
+            os.replace(tmp, cache)
+        return {"source": "tuned", "rows": out_rows, "chosen": chosen}
 
     def debug_inject(self, flags: int):
         """Host-side fault injection (RT_FAULT_* flags) for tests."""

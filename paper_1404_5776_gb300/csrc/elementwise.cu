@@ -4,6 +4,8 @@
 // unitarity measure of eq. s_unit, and deterministic fixed-order reductions.
 #include <cmath>
 
+#include <cstring>
+
 #include "rt_elementwise.cuh"
 
 namespace rt {
@@ -843,6 +845,20 @@ void launch_poly_upper(const PolyTerms& C, int deg, const DevState* s, int which
   RT_CUDA_CHECK(cudaGetLastError());
 }
 
+// b = (float)a, complex, n elements (round to nearest)
+__global__ void k_z2c(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+void launch_z2c(const double2* a, float2* b, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_z2c<<<(unsigned)g, 256, 0, st>>>(a, b, n);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
 // z = x + a*y (complex FP64 vectors of n elements)
 __global__ void k_zaxpy(double2* __restrict__ z, const double2* __restrict__ x, const double2* __restrict__ y, double a,
                         int64_t n) {
@@ -951,20 +967,33 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) k_field_poly(PolyTerms V, int
                                                                 float2* __restrict__ dU, float2* __restrict__ dUH,
                                                                 int64_t nnzb, const int32_t* __restrict__ rowidx,
                                                                 const int32_t* __restrict__ col, int B, int rs,
-                                                                int stochastic, int planar) {
+                                                                int stochastic, int planar, PolyTerms32 T,
+                                                                int tail) {
   __shared__ float2 tiles[POLY_WARPS][13 * 13];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double E = s->E[which];
+  const float Ef = (float)E;
   const int64_t step = s->step;
   const int NE = B * B;
   for (int64_t q = (int64_t)blockIdx.x * POLY_WARPS + warp; q < nnzb; q += (int64_t)gridDim.x * POLY_WARPS) {
     const bool diag = rowidx[q] == col[q];
     for (int e = lane; e < NE; e += 32) {
       const int64_t idx = q * NE + e;
-      double2 u = V.v[deg][idx];
-      for (int m = deg - 1; m >= 0; --m) {
-        const double2 vm = V.v[m][idx];
-        u = make_double2(fma(u.x, E, vm.x), fma(u.y, E, vm.y));
+      double2 u;
+      if (tail && deg >= 1) {
+        float2 t = T.v[deg][idx];
+        for (int m = deg - 1; m >= 1; --m) {
+          const float2 vm = T.v[m][idx];
+          t = make_float2(fmaf(t.x, Ef, vm.x), fmaf(t.y, Ef, vm.y));
+        }
+        const double2 v0 = V.v[0][idx];
+        u = make_double2(fma((double)t.x, E, v0.x), fma((double)t.y, E, v0.y));
+      } else {
+        u = V.v[deg][idx];
+        for (int m = deg - 1; m >= 0; --m) {
+          const double2 vm = V.v[m][idx];
+          u = make_double2(fma(u.x, E, vm.x), fma(u.y, E, vm.y));
+        }
       }
       if (U) U[idx] = u;
       if (dU) store_du_block(tiles[warp], u, e, B, rs, q, diag, stochastic, step, idx, planar ? nullptr : dU);
@@ -978,13 +1007,19 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) k_field_poly(PolyTerms V, int
 
 void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which, double2* U, float2* dU,
                        float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st,
-                       bool stochastic, bool planar) {
+                       bool stochastic, bool planar, const PolyTerms32* tail) {
   RT_REQUIRE(deg >= 0 && deg < RT_MAX_POLY, RT_EINTERNAL, "field polynomial degree out of range");
   RT_REQUIRE(B <= 13, RT_EINTERNAL, "block size above 13");
   RT_REQUIRE(!planar || B == 13, RT_EINTERNAL, "column-planar blocks are 13-function blocks");
+  RT_REQUIRE(!tail || (dU && !U && stochastic), RT_EINTERNAL,
+             "the FP32 tail serves the stochastically rounded dU only");
   if (nnzb == 0) return;
+  PolyTerms32 T;
+  memset(&T, 0, sizeof(T));
+  if (tail) T = *tail;
   k_field_poly<<<(unsigned)poly_grid(nnzb), POLY_WARPS * 32, 0, st>>>(V, deg, s, which, U, dU, dUH, nnzb, rowidx, col,
-                                                                      B, rs32(B), stochastic ? 1 : 0, planar ? 1 : 0);
+                                                                      B, rs32(B), stochastic ? 1 : 0, planar ? 1 : 0,
+                                                                      T, tail ? 1 : 0);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -12,7 +12,9 @@
 // All work runs on an internal stream ordered against the caller's stream with
 // events; a step is captured once in a CUDA graph and replayed.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <limits>
 #include <map>
@@ -96,9 +98,15 @@ struct Sys {
   bool ref_ready = false;         // K_ref and its traces are formed
   bool r_ready = false;           // R (constant U) or the Bp (field polynomial) match K_ref and U
   std::vector<double2*> Bp;       // coefficients of R(E) on P_K (Bp[0] includes -K_ref)
+  double2** d_bp = nullptr;       // device table of the Bp (the K' epilogue evaluates R(E) from them)
+  std::vector<float2*> V32;       // reference split: FP32 copies of V_1..V_deg (V32[0] null), the FP32 tail
+                                  // of the per-step Horner pass for U(E) - I
   float2 *dUr = nullptr, *dUHr = nullptr;  // U - I stochastically rounded to FP32, and its block dagger
   bool u64_stale = false;         // the FP64 U is not formed per step (field polynomial, reference split)
   bool planar = false;            // dUr and Wf column-planar: the packed-FMA products of the reference split
+  std::vector<float2*> Kfk;       // reference split, per kick: dK rounded to FP32 (kick 0 shares Kf); the
+                                  // delta-sandwich epilogue rewrites it with every step
+  std::vector<float2*> Mfk, Wfk;  // reference split, per kick: M and W = dK + M (kick 0 shares Mf, Wf)
   // maps
   int32_t *u_to_t = nullptr, *a_to_s = nullptr, *a_to_h = nullptr, *k_to_sT = nullptr, *k_to_hT = nullptr;
   int32_t *u_to_sinv = nullptr, *k_to_sinv = nullptr, *u_to_s = nullptr, *k_to_m = nullptr, *m_to_k = nullptr;
@@ -114,6 +122,28 @@ struct Sys {
   int sinv_iters = 0;
   double sinv_resid = 0.0;
   std::string sinv_status;
+};
+
+// Grouped products of the reference split (one launch per product and block
+// size across all (system, kick) pairs) and their launch shapes
+constexpr int RT_N_STAGES = 4;  // 13-function M, 13-function K', 4-function M, 4-function K'
+inline int stage_of(int B, bool kstage) { return (B == 13 ? 0 : 2) + (kstage ? 1 : 0); }
+struct LaunchShape {
+  int stages = 0;      // 13-function kernel: stages per warp (0 = 2)
+  int persistent = 0;  // one resident wave of CTAs walking the items
+};
+struct StageGroup {
+  GemmArgs* d_args = nullptr;  // device table: one entry per (system, kick) pair
+  int2* d_items = nullptr;     // (pair, item) of every item, largest pairs first
+  GemmArgs single{};           // the one pair's arguments (a stage with one pair launches without tables)
+  std::vector<GemmArgs> host;  // host copy of the table (the tuner redirects the K' outputs)
+  size_t out_bytes = 0, kf_bytes = 0;  // largest K' output and FP32 copy of one pair
+  int64_t n_items = 0;
+  int n_groups = 0;
+  int B = 0;
+  int planar = 0;
+  bool bdag = false;
+  double flops = 0, bytes = 0;
 };
 
 }  // namespace rt
@@ -156,10 +186,16 @@ struct rt_ctx {
   };
   std::vector<PendingEv> pending;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+  // grouped products and the launch shapes the tuner chose
+  rt::LaunchShape shape[rt::RT_N_STAGES];
+  rt::StageGroup groups[rt::RT_N_STAGES];
+  bool groups_built = false;
   bool poisoned = false;
   bool unrecoverable = false;  // a drain of copies in flight gave up: shared memory may have been written late
   std::string err;
 };
+
+static void check_device_error(rt_ctx* c);
 
 namespace rt {
 
@@ -277,8 +313,10 @@ static double gemm_bytes(const Sys&, const TripleInfo& ti, bool cplx, bool fp32)
   return bpe * (double)(ti.true_elems_a + ti.true_elems_b + ti.true_elems_c);
 }
 
-static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cplx, bool ad, bool bd, Epilogue epi,
-                 GemmArgs g, const Pattern* C) {
+// The arguments of one block product, completed from its triple list and
+// output pattern, with the overlap checks of its buffers.
+static GemmArgs prepared(rt_ctx* c, Sys& s, TripleInfo& ti, bool fp32, bool cplx, Epilogue epi, GemmArgs g,
+                         const Pattern* C) {
   g.item_blk = ti.t.item_blk;
   g.ptr = ti.t.ptr;
   g.ab = ti.t.ab;
@@ -312,10 +350,21 @@ static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cpl
                "block product output overlaps an operand");
     RT_REQUIRE(!overlaps(g.U, nU, g.A, nA) && !overlaps(g.U, nU, g.B, nB), RT_EINTERNAL,
                "block product accumulator overlaps an operand");
+    const size_t nF = C ? (size_t)C->nnzb * sb32(s.B) * 8 : 1;
+    RT_REQUIRE(!overlaps(g.kf32, nF, g.A, nA) && !overlaps(g.kf32, nF, g.B, nB), RT_EINTERNAL,
+               "FP32 copy of the output overlaps an operand");
   }
+  return g;
+}
+
+static void gemm(rt_ctx* c, Sys& s, int cls, TripleInfo& ti, bool fp32, bool cplx, bool ad, bool bd, Epilogue epi,
+                 GemmArgs g, const Pattern* C) {
+  g = prepared(c, s, ti, fp32, cplx, epi, g, C);
   int B = s.B;
   RT_REQUIRE(!g.a_planar || (fp32 && cplx && B == 13 && !ti.tiles.built), RT_EINTERNAL,
              "column-planar operands belong to the packed CUDA-core products");
+  RT_REQUIRE(!g.kf32 || (fp32 && cplx && epi == EPI_DELTA_SANDWICH && !ti.tiles.built), RT_EINTERNAL,
+             "the FP32 copy of K' comes from the CUDA-core delta sandwich");
   if (fp32 && cplx && B == 13 && !ad && !bd && ti.tiles.built && (epi == EPI_STORE || epi == EPI_DELTA_SANDWICH)) {
     g.tl_n = ti.tiles.n_tiles;
     g.tl_item0 = ti.tiles.item0;
@@ -588,6 +637,26 @@ static void setup_system(rt_ctx* c, Sys& s, const rt_system& in) {
     s.tref = c->arena.get_n<double>(8);
     for (int k = 0; k < p.n_kick; ++k) s.dK.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
     s.dk_fresh.assign(p.n_kick, 0);
+    if (p.full_step) {
+      // coefficients B_0..B_2deg of R(E), formed with the reference (first step)
+      const int deg = p.taylor_terms - 1;
+      RT_REQUIRE(2 * deg < RT_MAX_POLY, RT_EINVAL, "taylor_terms too large for the reference split");
+      for (int q = 0; q <= 2 * deg; ++q) s.Bp.push_back(c->arena.get_n<double2>(nvals(s, s.pK)));
+      s.d_bp = c->arena.get_n<double2*>(s.Bp.size());
+      RT_CUDA_CHECK(
+          cudaMemcpyAsync(s.d_bp, s.Bp.data(), sizeof(double2*) * s.Bp.size(), cudaMemcpyHostToDevice, c->ws));
+    }
+    s.Kfk.push_back(s.Kf);
+    s.Mfk.push_back(s.Mf);
+    s.Wfk.push_back(s.Wf);
+    for (int k = 1; k < p.n_kick; ++k) {
+      s.Kfk.push_back(c->arena.get_n<float2>(nvals32(s, s.pK)));
+      s.Mfk.push_back(c->arena.get_n<float2>(nvals32(s, s.pM)));
+      s.Wfk.push_back(c->arena.get_n<float2>(nvals32(s, s.pM)));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Kfk.back(), 0, sizeof(float2) * nvals32(s, s.pK), c->ws));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Mfk.back(), 0, sizeof(float2) * nvals32(s, s.pM), c->ws));
+      RT_CUDA_CHECK(cudaMemsetAsync(s.Wfk.back(), 0, sizeof(float2) * nvals32(s, s.pM), c->ws));
+    }
     s.dUr = c->arena.get_n<float2>(nvals32(s, s.pU));
     RT_CUDA_CHECK(cudaMemsetAsync(s.dUr, 0, sizeof(float2) * nvals32(s, s.pU), c->ws));
     if (s.B == 13) {  // the 13-function kernels read a pre-transposed dagger
@@ -919,6 +988,14 @@ static void build_field_poly(rt_ctx* c, Sys& s) {
     }
     prev.assign(out.begin(), out.begin() + n + 1);
   }
+  if (p.incremental && p.precision == RT_FP32) {
+    // FP32 copies of V_1..V_deg for the per-step pass of the reference split
+    if (s.V32.empty()) {
+      s.V32.push_back(nullptr);
+      for (int m = 1; m <= deg; ++m) s.V32.push_back(c->arena.get_n<float2>(nU));
+    }
+    for (int m = 1; m <= deg; ++m) launch_z2c(s.V[m], s.V32[m], (int64_t)nU, c->ws);
+  }
 }
 
 static void build_propagator(rt_ctx* c, Sys& s, bool fp32) {
@@ -1140,8 +1217,17 @@ static void prepare_reference(rt_ctx* c, Sys& s) {
   for (size_t k = 0; k < s.dk_fresh.size(); ++k) {
     if (s.dk_fresh[k]) continue;
     launch_zaxpy(s.dK[k], s.K[k], s.Kref, -1.0, (int64_t)nv, c->ws);
+    launch_d2f_pad((const double*)s.dK[k], (float*)s.Kfk[k], s.pK->nnzb, s.B, true, c->ws);
     s.dk_fresh[k] = 1;
   }
+}
+
+// With the field polynomial on the CUDA cores, the K' epilogue evaluates
+// R(E) = sum_p E^p B_p itself (the tensor-core kernel reads R from the
+// separate Horner pass).
+static bool r_fused(const rt_ctx* c, const Sys& s) {
+  return incremental(c) && c->p.full_step && s.d_bp != nullptr &&
+         !(c->p.precision == RT_FP32 && c->p.tensor_cores && s.B == 13);
 }
 
 // The propagator of a reference-split step: dU = U - I stochastically rounded
@@ -1154,17 +1240,23 @@ static void reference_split_propagator(rt_ctx* c, Sys& s) {
     const int deg2 = 2 * (c->p.taylor_terms - 1);
     for (int q = 0; q <= deg2; ++q) C.v[q] = s.Bp[q];
     const double nK = (double)nvals(s, s.pK);
-    run(c, PC_POLY, 0, 16.0 * nK * (deg2 + 2) / 2.0, [&] {  // upper blocks: read B_0..B_deg2, write R
-      launch_poly_upper(C, deg2, c->dstate, 0, s.Rm, s.pK->nnzb, s.pK->rowidx, s.pK->col, s.B, c->ws);
-    });
+    if (!r_fused(c, s))
+      run(c, PC_POLY, 0, 16.0 * nK * (deg2 + 2) / 2.0, [&] {  // upper blocks: read B_0..B_deg2, write R
+        launch_poly_upper(C, deg2, c->dstate, 0, s.Rm, s.pK->nnzb, s.pK->rowidx, s.pK->col, s.B, c->ws);
+      });
     PolyTerms V;
     memset(&V, 0, sizeof(V));
     const int deg = c->p.taylor_terms - 1;
     for (int m = 0; m <= deg; ++m) V.v[m] = s.V[m];
     const double nU = (double)nvals(s, s.pU);
-    run(c, PC_POLY, 0, 16.0 * nU * (deg + 1) + 16.0 * nU, [&] {  // read V_0..V_deg, write dU and dU^dagger
+    PolyTerms32 T;
+    memset(&T, 0, sizeof(T));
+    const bool tail = (int)s.V32.size() == deg + 1;
+    for (int m = 1; m <= deg && tail; ++m) T.v[m] = s.V32[m];
+    // read V_0 (FP64) and V_1..V_deg (FP32 tail), write dU and dU^dagger
+    run(c, PC_POLY, 0, 16.0 * nU + (tail ? 8.0 : 16.0) * nU * deg + 16.0 * nU, [&] {
       launch_field_poly(V, deg, c->dstate, 0, nullptr, s.dUr, s.dUHr, s.pU->nnzb, s.pU->rowidx, s.pU->col, s.B,
-                        c->ws, true, s.planar);
+                        c->ws, true, s.planar, tail ? &T : nullptr);
     });
     s.u64_stale = true;
   } else {
@@ -1177,48 +1269,288 @@ static void reference_split_propagator(rt_ctx* c, Sys& s) {
 // dK' = dK + R + M + N with M = cut(dU dK), W = dK + M, N = cut(W dU^dagger)
 // (FP32 products of the small dK, every part summed in FP64); R in FP64
 // (constant, or R(E) formed for this step's field by the propagator pass).
+// The two products of a reference-split step for one kick slot:
+//   M  = cut(dU dK) on P_M, with W = dK + M from the same epilogue;
+//   dK' = dK + R + M + cut(W dU^dagger) on the upper blocks of P_K (mirrored),
+//        leaving dK' rounded to FP32 for the next step's M (CUDA cores).
+// 13-function blocks read the pre-transposed dagger; the 4-function kernel
+// transposes while loading.
+static GemmArgs m_args(Sys& s, int kick) {
+  GemmArgs g = args(s.dUr, s.Kfk[kick], s.Mfk[kick]);
+  g.base = s.dK[kick];
+  g.U = s.Wfk[kick];
+  g.add_map = s.m_to_k;
+  g.a_planar = s.planar ? 1 : 0;  // dU in, W out column-planar
+  return g;
+}
+static GemmArgs k_args(rt_ctx* c, Sys& s, int kick, int slot, bool kf_by_epilogue) {
+  const bool pre_t = s.dUHr != nullptr;
+  GemmArgs g = args(s.Wfk[kick], pre_t ? s.dUHr : s.dUr, s.dK[kick]);
+  g.herm_max = &c->dstate->herm_bits[slot];
+  g.base = s.dK[kick];
+  g.addend = s.Mfk[kick];
+  g.add_map = s.k_to_m;
+  if (r_fused(c, s)) {
+    g.rpoly = s.d_bp;
+    g.rdeg = (int)s.Bp.size() - 1;
+    g.poly_E = reinterpret_cast<const double*>(reinterpret_cast<const char*>(c->dstate) + offsetof(DevState, E));
+  } else {
+    g.base2 = s.Rm;
+  }
+  g.a_planar = s.planar ? 1 : 0;  // W column-planar
+  g.kf32 = kf_by_epilogue ? s.Kfk[kick] : nullptr;
+  return g;
+}
+
+// One kick slot, its own launches (the tensor-core products, or a context
+// that does not group its products).
 static void sandwich_incremental(rt_ctx* c, Sys& s, int kick, int slot) {
   TripleInfo& tM = triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
   TripleInfo& tK = triples_for(c, s, s.pM, false, s.pU, true, s.pK, true);
-  double2* dK = s.dK[kick];
-  run(c, PC_MISC, 0, 0, [&] { launch_d2f_pad((const double*)dK, (float*)s.Kf, s.pK->nnzb, s.B, true, c->ws); });
-  if (s.B == 13) {
-    GemmArgs g = args(s.dUr, s.Kf, s.Mf);
-    g.base = dK;  // W = dK + M from the same epilogue
-    g.U = s.Wf;
-    g.add_map = s.m_to_k;
-    g.a_planar = s.planar ? 1 : 0;  // dU in, W out column-planar
-    gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, g, s.pM);
-  } else {
-    gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, args(s.dUr, s.Kf, s.Mf), s.pM);
-    run(c, PC_MISC, 0, 0, [&] { launch_delta_w(dK, s.m_to_k, s.Mf, s.Wf, s.pM->nnzb, s.B, c->ws); });
-  }
-  // 13-function blocks read the pre-transposed dagger; the 4-function kernel
-  // transposes while loading
+  // the CUDA-core delta sandwich leaves dK' rounded to FP32 for the next step
+  // (formed with dK itself); the tensor-core kernel does not, so round here
+  const bool kf_by_epilogue = !tK.tiles.built;
+  if (!kf_by_epilogue)
+    run(c, PC_MISC, 0, 0, [&] {
+      launch_d2f_pad((const double*)s.dK[kick], (float*)s.Kfk[kick], s.pK->nnzb, s.B, true, c->ws);
+    });
+  GemmArgs gm = m_args(s, kick);
+  gm.stages = c->shape[stage_of(s.B, false)].stages;
+  gm.persistent = c->shape[stage_of(s.B, false)].persistent;
+  gemm(c, s, PC_UK, tM, true, true, false, false, EPI_STORE, gm, s.pM);
   const bool pre_t = s.dUHr != nullptr;
-  GemmArgs g = args(s.Wf, pre_t ? s.dUHr : s.dUr, dK);
-  g.herm_max = &c->dstate->herm_bits[slot];
-  g.base = dK;
-  g.addend = s.Mf;
-  g.add_map = s.k_to_m;
-  g.base2 = s.Rm;
-  g.a_planar = s.planar ? 1 : 0;  // W column-planar
-  gemm(c, s, PC_MUDAG, tK, true, true, false, !pre_t, EPI_DELTA_SANDWICH, g, s.pK);
+  GemmArgs gk = k_args(c, s, kick, slot, kf_by_epilogue);
+  gk.stages = c->shape[stage_of(s.B, true)].stages;
+  gk.persistent = c->shape[stage_of(s.B, true)].persistent;
+  gemm(c, s, PC_MUDAG, tK, true, true, false, !pre_t, EPI_DELTA_SANDWICH, gk, s.pK);
+}
+
+// Grouped products: every (system, kick) pair of one block size multiplied
+// by one launch per product (M, then K'), the pairs ordered by their triple
+// counts, largest first, so that the launch ends on the smallest products.
+// Built once, outside graph capture (the argument tables live on the device).
+static bool groups_apply(const rt_ctx* c) {
+  if (!incremental(c)) return false;
+  for (const auto& sp : c->sys)
+    if (sp->B != 13 && sp->B != 4) return false;
+  return !(c->p.tensor_cores && c->p.precision == RT_FP32);
+}
+
+static void build_groups(rt_ctx* c) {
+  if (c->groups_built || !groups_apply(c)) return;
+  for (int st = 0; st < RT_N_STAGES; ++st) {
+    const bool kstage = st & 1;
+    const int B = st < 2 ? 13 : 4;
+    c->groups[st] = StageGroup();
+    struct Entry {
+      GemmArgs g;
+      int64_t triples;
+      double flops, bytes;
+      int sys;
+    };
+    std::vector<Entry> es;
+    int slot = 0, si = 0;
+    for (auto& sp : c->sys) {
+      Sys& s = *sp;
+      ++si;
+      for (int k = 0; k < c->p.n_kick; ++k, ++slot) {
+        if (s.B != B) continue;
+        TripleInfo& ti = kstage ? triples_for(c, s, s.pM, false, s.pU, true, s.pK, true)
+                                : triples_for(c, s, s.pU, false, s.pK, false, s.pM, false);
+        GemmArgs g = kstage ? prepared(c, s, ti, true, true, EPI_DELTA_SANDWICH, k_args(c, s, k, slot, true), s.pK)
+                            : prepared(c, s, ti, true, true, EPI_STORE, m_args(s, k), s.pM);
+        g.tri = nullptr;  // host view: not used on the device
+        es.push_back({g, ti.t.n_triples, gemm_flops(ti, true), gemm_bytes(s, ti, true, true), si});
+        if (kstage) {
+          c->groups[st].out_bytes = std::max(c->groups[st].out_bytes, nvals(s, s.pK) * sizeof(double2));
+          c->groups[st].kf_bytes = std::max(c->groups[st].kf_bytes, nvals32(s, s.pK) * sizeof(float2));
+        }
+      }
+    }
+    StageGroup& G = c->groups[st];
+    const size_t ob = G.out_bytes, kb = G.kf_bytes;
+    G = StageGroup();
+    G.out_bytes = ob;
+    G.kf_bytes = kb;
+    if (es.empty()) continue;
+    // systems by their triple counts, largest first; the kicks of one system
+    // (the same triple list and the same dU) interleaved item by item, so that
+    // their warps read each dU block at about the same time
+    std::stable_sort(es.begin(), es.end(), [](const Entry& x, const Entry& y) {
+      return x.triples != y.triples ? x.triples > y.triples : x.sys < y.sys;
+    });
+    std::vector<GemmArgs> tab;
+    std::vector<int2> items;
+    for (size_t i = 0; i < es.size(); ++i) {
+      tab.push_back(es[i].g);
+      G.flops += es[i].flops;
+      G.bytes += es[i].bytes;
+    }
+    for (size_t i = 0; i < es.size();) {
+      size_t j = i;
+      while (j < es.size() && es[j].sys == es[i].sys) ++j;  // the kicks of one system
+      for (int64_t it = 0; it < es[i].g.n_items; ++it)
+        for (size_t e = i; e < j; ++e) items.push_back(make_int2((int)e, (int)it));
+      i = j;
+    }
+    RT_REQUIRE(items.size() < (size_t)INT32_MAX, RT_EINVAL, "too many output blocks in one grouped product");
+    if (tab.size() > 1) {
+      G.d_args = c->arena.get_n<GemmArgs>(tab.size());
+      G.d_items = c->arena.get_n<int2>(items.size() + 1);
+      RT_CUDA_CHECK(
+          cudaMemcpyAsync(G.d_args, tab.data(), sizeof(GemmArgs) * tab.size(), cudaMemcpyHostToDevice, c->ws));
+      if (!items.empty())
+        RT_CUDA_CHECK(
+            cudaMemcpyAsync(G.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, c->ws));
+      RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    }
+    G.n_groups = (int)tab.size();
+    G.single = tab[0];
+    G.host = tab;
+    G.n_items = (int64_t)items.size();
+    G.B = B;
+    G.planar = tab[0].a_planar;
+    G.bdag = kstage && B == 4;  // the 4-function kernel transposes dU while loading
+  }
+  c->groups_built = true;
+}
+
+// The launch of one grouped stage: the launch-level arguments carry the
+// tables, the item count and the launch shape; every product's own
+// arguments come from its table entry.
+static GemmArgs group_launch_args(const rt_ctx* c, int st, const StageGroup& G) {
+  GemmArgs g;
+  if (G.n_groups == 1) {
+    g = G.single;
+    g.wait_ns = c->wait_ns;  // the budget of this launch (a fault injection may have set it)
+    g.stages = c->shape[st].stages;
+    g.persistent = c->shape[st].persistent;
+    return g;
+  }
+  memset(&g, 0, sizeof(g));
+  g.grp = G.d_args;
+  g.gitems = G.d_items;
+  g.n_items = G.n_items;
+  g.zero = c->zero32;
+  g.err = c->d_err;
+  g.wait_ns = c->wait_ns;
+  g.a_planar = G.planar;
+  g.stages = c->shape[st].stages;
+  g.persistent = c->shape[st].persistent;
+  return g;
+}
+
+// Launch shapes the tuner tries per stage: stages per warp (13-function
+// kernel: 2 or 3) and one-shot or persistent grids.
+static std::vector<LaunchShape> shape_candidates(int st) {
+  if (st < 2) return {{0, 0}, {0, 1}, {3, 0}, {3, 1}};
+  return {{0, 0}, {0, 1}};
+}
+
+// Times every candidate shape of every grouped stage on the context's own
+// products (one warm-up launch, then `reps` launches between CUDA events) and
+// keeps the fastest.  The M products write only M and W (formed again by the
+// next step); the K' products write into scratch copies of their outputs, so
+// the density is left as it was.
+static void autotune(rt_ctx* c, int reps, std::vector<std::array<int, 4>>* rows, std::vector<double>* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RT_CUDA_CHECK(cudaEventCreate(&e0));
+  RT_CUDA_CHECK(cudaEventCreate(&e1));
+  try {
+    for (int st = 0; st < RT_N_STAGES; ++st) {
+      const StageGroup& G = c->groups[st];
+      if (G.n_items == 0) continue;
+      const bool kstage = st & 1;
+      Scratch tmp(c);
+      GemmArgs base_args = group_launch_args(c, st, G);
+      if (kstage) {
+        // redirect K', its FP32 copy and the hermiticity record to scratch
+        double2* kout = tmp.get_n<double2>(G.out_bytes / sizeof(double2) + 1);
+        float2* fout = tmp.get_n<float2>(G.kf_bytes / sizeof(float2) + 1);
+        unsigned long long* hm = tmp.get_n<unsigned long long>(1);
+        std::vector<GemmArgs> tab = G.host;
+        for (GemmArgs& a : tab) {
+          a.C = kout;
+          a.kf32 = fout;
+          a.herm_max = hm;
+        }
+        if (G.n_groups == 1) {
+          base_args.C = kout;
+          base_args.kf32 = fout;
+          base_args.herm_max = hm;
+        } else {
+          GemmArgs* d_tab = tmp.get_n<GemmArgs>(tab.size());
+          RT_CUDA_CHECK(
+              cudaMemcpyAsync(d_tab, tab.data(), sizeof(GemmArgs) * tab.size(), cudaMemcpyHostToDevice, c->ws));
+          base_args.grp = d_tab;
+        }
+      }
+      double best = 1e300;
+      LaunchShape pick = c->shape[st];
+      for (const LaunchShape& sh : shape_candidates(st)) {
+        GemmArgs g = base_args;
+        g.stages = sh.stages;
+        g.persistent = sh.persistent;
+        auto launch = [&] {
+          launch_gemm(G.B, true, true, false, G.bdag, kstage ? EPI_DELTA_SANDWICH : EPI_STORE, g, c->ws);
+        };
+        launch();
+        RT_CUDA_CHECK(cudaEventRecord(e0, c->ws));
+        for (int r = 0; r < reps; ++r) launch();
+        RT_CUDA_CHECK(cudaEventRecord(e1, c->ws));
+        RT_CUDA_CHECK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        RT_CUDA_CHECK(cudaEventElapsedTime(&t, e0, e1));
+        const double per = (double)t / reps;
+        if (rows) rows->push_back({st, sh.stages == 0 ? 2 : sh.stages, sh.persistent, 0});
+        if (ms) ms->push_back(per);
+        if (per < best) {
+          best = per;
+          pick = sh;
+        }
+      }
+      c->shape[st] = pick;
+      if (rows)
+        for (auto& r : *rows)
+          if (r[0] == st) r[3] = (r[1] == (pick.stages == 0 ? 2 : pick.stages) && r[2] == pick.persistent) ? 1 : 0;
+      ::check_device_error(c);
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->graph_dirty = true;
+}
+
+static void grouped_stage(rt_ctx* c, int st) {
+  const StageGroup& G = c->groups[st];
+  if (G.n_items == 0) return;
+  const bool kstage = st & 1;
+  GemmArgs g = group_launch_args(c, st, G);
+  run(c, kstage ? PC_MUDAG : PC_UK, G.flops, G.bytes, [&] {
+    launch_gemm(G.B, true, true, false, G.bdag, kstage ? EPI_DELTA_SANDWICH : EPI_STORE, g, c->ws);
+  });
 }
 
 static void enqueue_step(rt_ctx* c) {
   run(c, PC_MISC, 0, 0, [&] { launch_begin_step(c->dstate, c->field, c->p.dt, c->n_slots, c->ws); });
   int slot = 0;
+  const bool grouped = c->groups_built;
   for (auto& sp : c->sys) {
     Sys& s = *sp;
     if (incremental(c)) reference_split_propagator(c, s);
     else if (c->p.full_step) build_propagator(c, s, c->p.precision == RT_FP32);
-    for (int k = 0; k < c->p.n_kick; ++k) {
+    for (int k = 0; k < c->p.n_kick && !grouped; ++k) {
       if (incremental(c)) sandwich_incremental(c, s, k, slot + k);
       else sandwich(c, s, k, slot + k);
     }
     slot += c->p.n_kick;
   }
+  if (grouped)
+    for (int st : {0, 2, 1, 3}) grouped_stage(c, st);  // every M product, then every K' product
   run(c, PC_MISC, 0, 0, [&] { launch_end_step(c->dstate, c->p.dt, c->ws); });
   slot = 0;
   for (auto& sp : c->sys) {
@@ -1452,7 +1784,7 @@ rt_status rt_default_params(rt_params* p) {
   p->hot_step_iters = 2;
   p->hot_fp64_iters = 1;
   p->tensor_cores = 0;
-  p->packed_fma = 0;
+  p->packed_fma = 1;
   p->precision = RT_FP64;
   p->full_step = 1;
   p->n_kick = 1;
@@ -1695,6 +2027,49 @@ rt_status rt_propagator(rt_ctx* c, double t) {
   });
 }
 
+rt_status rt_autotune(rt_ctx* c, int32_t reps, int32_t max_rows, int32_t* n_rows, int32_t* rows, double* ms) {
+  return guarded(c, [&] {
+    RT_REQUIRE(reps >= 1 && reps <= 100, RT_EINVAL, "reps must be 1..100");
+    RT_REQUIRE(max_rows >= 0 && (max_rows == 0 || (rows && ms)), RT_EINVAL, "bad output buffers");
+    RT_REQUIRE(groups_apply(c), RT_ESTATE,
+               "the tuner times the reference split's CUDA-core products (incremental = 1, tensor_cores = 0, "
+               "block sizes 4 and 13)");
+    build_groups(c);
+    std::vector<std::array<int, 4>> r;
+    std::vector<double> t;
+    autotune(c, reps, &r, &t);
+    if (n_rows) *n_rows = (int32_t)r.size();
+    for (size_t i = 0; i < r.size() && (int32_t)i < max_rows; ++i) {
+      for (int k = 0; k < 4; ++k) rows[4 * i + k] = r[i][k];
+      ms[i] = t[i];
+    }
+    return RT_OK;
+  });
+}
+
+rt_status rt_set_launch_shape(rt_ctx* c, int32_t stage, int32_t stages, int32_t persistent) {
+  return guarded(c, [&] {
+    RT_REQUIRE(stage >= 0 && stage < RT_N_STAGES, RT_EINVAL, "stage must be 0..3");
+    RT_REQUIRE(stages == 2 || (stages == 3 && stage < 2), RT_EINVAL,
+               "stages per warp: 2, or 3 for the 13-function stages");
+    RT_REQUIRE(persistent == 0 || persistent == 1, RT_EINVAL, "persistent must be 0 or 1");
+    c->shape[stage].stages = stages == 2 ? 0 : stages;
+    c->shape[stage].persistent = persistent;
+    c->graph_dirty = true;
+    return RT_OK;
+  });
+}
+
+rt_status rt_get_launch_shape(rt_ctx* c, int32_t stage, int32_t* stages, int32_t* persistent) {
+  return guarded(c, [&] {
+    RT_REQUIRE(stage >= 0 && stage < RT_N_STAGES, RT_EINVAL, "stage must be 0..3");
+    RT_REQUIRE(stages && persistent, RT_EINVAL, "NULL output");
+    *stages = c->shape[stage].stages == 0 ? 2 : c->shape[stage].stages;
+    *persistent = c->shape[stage].persistent;
+    return RT_OK;
+  });
+}
+
 rt_status rt_step(rt_ctx* c, int32_t n) {
   return guarded(c, [&] {
     RT_REQUIRE(n >= 0, RT_EINVAL, "n must be non-negative");
@@ -1705,6 +2080,7 @@ rt_status rt_step(rt_ctx* c, int32_t n) {
     if (n == 0) return RT_OK;
     if (incremental(c))
       for (auto& sp : c->sys) prepare_reference(c, *sp);
+    build_groups(c);
     if (c->inject & RT_FAULT_WAIT_TIMEOUT_0) {
       // one step, launched directly, with a zero wait budget; the error word
       // is read back here so that this call reports the expiry

@@ -66,13 +66,22 @@ constexpr int RT_MAX_POLY = 32;
 struct PolyTerms {
   const double2* v[RT_MAX_POLY];
 };
+// FP32 copies of V_1..V_deg (v[0] unused) for the FP32 tail of the Horner pass
+struct PolyTerms32 {
+  const float2* v[RT_MAX_POLY];
+};
+// b = (float)a for n complex values (dense, same element order)
+void launch_z2c(const double2* a, float2* b, int64_t n, cudaStream_t st);
 // U = sum_{m<=deg} E^m V_m at E = s->E[which] (Horner, FP64); writes U (FP64, if non-null) and/or
 // dU = U - I with its per-block conjugate transpose dUH in FP32 (padded rows), if non-null, rounded to
 // nearest or, with `stochastic`, stochastically (draws keyed on s->step and the element); with `planar`
 // (13-function blocks) dU is written column-planar as in launch_round_u_sr
+// tail (with dU only, stochastic): U = V_0 + E q(E), q(E) = sum_{m>=1} E^(m-1) V_m by Horner in FP32 over
+// tail->v[1..deg] and V_0 + E q in FP64 (two FP64 FMAs per element instead of 2 deg); q's FP32 rounding
+// is far below the stochastic rounding of dU that follows
 void launch_field_poly(const PolyTerms& V, int deg, const DevState* s, int which, double2* U, float2* dU,
                        float2* dUH, int64_t nnzb, const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st,
-                       bool stochastic = false, bool planar = false);
+                       bool stochastic = false, bool planar = false, const PolyTerms32* tail = nullptr);
 // R = sum_{p<=deg} E^p C_p at E = s->E[which] (Horner, FP64) on the upper blocks of a pattern
 void launch_poly_upper(const PolyTerms& C, int deg, const DevState* s, int which, double2* R, int64_t nnzb,
                        const int32_t* rowidx, const int32_t* col, int B, cudaStream_t st);

@@ -180,6 +180,18 @@ struct GemmArgs {
   int* err;                 // device error word: the largest code of a bounded wait that gave up
                             // (1: wait expired, copies drained; 2: the drain expired too)
   long long wait_ns;        // budget of one bounded wait (FP32 kernels), nanoseconds
+  // delta sandwich of the reference split with the field polynomial: R(E) =
+  // sum_p E^p B_p evaluated per element (Horner, FP64) in place of base2
+  const double2* const* rpoly;  // device table of B_0..B_rdeg (dense blocks on P_K), or null
+  int rdeg;
+  const double* poly_E;     // device address of the field value E
+  void* kf32;               // delta sandwich: also write K' rounded to FP32 (the FP32 block layout;
+                            // the B operand of the next step's first product), or null
+  // launch shape of the FP32 complex products (the tuner's choices)
+  int stages;               // 13-function kernel: stages per warp (0 = default 2, or 3)
+  int persistent;           // 1: at most one resident wave of CTAs, each walking items with a grid stride
+  const GemmArgs* grp;      // grouped launch: device array of per-product arguments, or null
+  const int2* gitems;       // grouped launch: (product, item within it) of every item
   int a_planar;             // complex 13-function FP32: A (and the W written by the delta
                             // form) column-planar, the packed-FMA kernel
   // row tiles (tensor-core products)

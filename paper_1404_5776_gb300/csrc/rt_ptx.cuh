@@ -25,6 +25,11 @@ __device__ __forceinline__ void tma_load_1d(void* sdst, const void* gsrc, unsign
       "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// order this thread's generic-proxy shared-memory writes before later
+// async-proxy (bulk copy) writes to the same shared memory
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
 __device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity) {
   unsigned done;
   asm volatile(

@@ -24,6 +24,8 @@
 //   * every wait on an mbarrier is bounded in time (the launch's budget, 2 s
 //     by default, read from the global timer): on expiry the kernel records an
 //     error code, waits (bounded) for its copies in flight and returns.
+#include <algorithm>
+
 #include "rt_internal.cuh"
 #include "rt_ptx.cuh"
 
@@ -139,11 +141,14 @@ static_assert(sizeof(Smem) <= 256, "control block");
 
 // dynamic shared memory per CTA (control block + every warp's stages) and the
 // CTAs per SM it leaves room for (227 KB per SM for CTAs)
-constexpr size_t SMEM_C = 256 + (size_t)WARPS * C_STAGES * (2 * Slot<float2>::STRIDE) * sizeof(float2);  // NT = 2
+// complex kernel with NS stages per warp (C_STAGES by default; the tuner also tries 3)
+constexpr size_t smem_c(int ns) { return 256 + (size_t)WARPS * ns * (2 * Slot<float2>::STRIDE) * sizeof(float2); }
+constexpr int minb_c(int ns) { return (int)((227 * 1024) / (smem_c(ns) + 1024)); }
+constexpr size_t SMEM_C = smem_c(C_STAGES);  // NT = 2
 constexpr size_t SMEM_R = 256 + (size_t)R_WARPS * R_STAGES * (4 * Slot<float>::STRIDE) * sizeof(float);  // NT = 4
 constexpr int MINB_C = (int)((227 * 1024) / (SMEM_C + 1024));
 constexpr int MINB_R = (int)((227 * 1024) / (SMEM_R + 1024));
-static_assert(MINB_C >= 1 && MINB_R >= 1, "stages do not fit in shared memory");
+static_assert(MINB_C >= 1 && MINB_R >= 1 && minb_c(3) >= 1, "stages do not fit in shared memory");
 
 // Elements of a 13 x 13 block handled by one lane in the per-element epilogues.
 constexpr int EPT = (NE + 31) / 32;
@@ -159,9 +164,10 @@ template <typename V, int NT, int S, typename F>
 __device__ __forceinline__ int stream_triples(V* wsm, uint64_t* bar, const V* __restrict__ A,
                                                const V* __restrict__ B, const V* __restrict__ Z,
                                                const int2* __restrict__ ab, int64_t t0, int64_t t1, int lane,
-                                               int h, long long wait_ns, F&& mac) {
+                                               int h, long long wait_ns, unsigned& phase, F&& mac) {
+  // phase, bit s: parity to wait for on stage s (carried from item to item:
+  // every stage's copies are waited for before an item ends)
   constexpr int WBUF = NT * Slot<V>::STRIDE;
-  unsigned phase = 0u;    // bit s: parity to wait for on stage s
   unsigned pending = 0u;  // bit s: copies in flight into stage s
   int64_t tnext = t0;     // first triple of the next group to issue
   int snext = 0;          // the stage it goes into
@@ -223,26 +229,10 @@ __device__ __forceinline__ int stream_triples(V* wsm, uint64_t* bar, const V* __
 // and the running sum takes re - re_n and im once per triple.  B stays in
 // the row layout; W (delta form) is written column-planar, since it is the A
 // operand of the next product.
-template <int EPI, bool PK>
-__global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
+template <int EPI, bool PK, int NS>
+__device__ __forceinline__ int c32_item(const GemmArgs& g, int64_t item, float2* wsm, uint64_t* bar,
+                                        unsigned& phase, int lane, int h, int c, long long wait_ns) {
   constexpr int NT = 2;
-  constexpr int WBUF = NT * Slot<float2>::STRIDE;  // one stage of one warp (float2)
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int h = lane >> 4;
-  const int c = lane & 15;
-  const int64_t item = (int64_t)blockIdx.x * WARPS + warp;
-  extern __shared__ __align__(128) unsigned char dyn_smem[];
-  Smem* ctl = reinterpret_cast<Smem*>(dyn_smem);
-  float2* wsm = reinterpret_cast<float2*>(dyn_smem + 256) + (size_t)warp * C_STAGES * WBUF;
-  if (item >= g.n_items) return;  // whole warp leaves together
-  uint64_t* bar = ctl->bar[warp];
-  if (lane == 0) {
-    for (int st = 0; st < C_STAGES; ++st) mbar_init(&bar[st], 1);
-    fence_mbar_init();
-  }
-  __syncwarp();
-
   float2 acc[BS];
 #pragma unroll
   for (int r = 0; r < BS; ++r) acc[r] = make_float2(0.f, 0.f);
@@ -253,9 +243,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
 
   int ok;
   if constexpr (PK) {
-    ok = stream_triples<float2, NT, C_STAGES>(
+    ok = stream_triples<float2, NT, NS>(
         wsm, bar, static_cast<const float2*>(g.A), static_cast<const float2*>(g.B),
-        static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns,
+        static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h, wait_ns, phase,
         [&](const float2* sA, const float2* sB) {
           const float* a = reinterpret_cast<const float*>(sA);
           uint64_t pre[NP], pren[NP], pim[NP];  // this triple's partial sums
@@ -307,9 +297,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
       if (2 * p + 1 < BS) acc[2 * p + 1] = make_float2(re.y, im.y);
     }
   } else {
-  ok = stream_triples<float2, NT, C_STAGES>(
+  ok = stream_triples<float2, NT, NS>(
       wsm, bar, static_cast<const float2*>(g.A), static_cast<const float2*>(g.B),
-      static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns,
+      static_cast<const float2*>(g.zero), g.ab, g.ptr[item], g.ptr[item + 1], lane, h, wait_ns, phase,
       [&](const float2* sA, const float2* sB) {
         float2 bcol[BS];
 #pragma unroll
@@ -332,10 +322,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
         }
       });
   }
-  if (ok != WAIT_OK) {
-    if (lane == 0 && g.err) atomicMax(g.err, ok);
-    return;
-  }
+  if (ok != WAIT_OK) return ok;
   // partial sums of the two groups to shared memory (every copy has landed)
   float2* part = wsm;  // [NT][BS][RS]
 #pragma unroll
@@ -450,6 +437,22 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
           val[k] = make_double2(val[k].x + rv.x, val[k].y + rv.y);
         }
       }
+    } else if (g.rpoly) {
+      // the same R at this step's field, R(E) = sum_p E^p B_p, by Horner here
+      const double E = *g.poly_E;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int e = lane + 32 * k;
+        if (e < NE) {
+          const int64_t idx = (int64_t)q * NE + e;
+          double2 rv = g.rpoly[g.rdeg][idx];
+          for (int p = g.rdeg - 1; p >= 0; --p) {
+            const double2 cp = g.rpoly[p][idx];
+            rv = make_double2(fma(rv.x, E, cp.x), fma(rv.y, E, cp.y));
+          }
+          val[k] = make_double2(val[k].x + rv.x, val[k].y + rv.y);
+        }
+      }
     }
 #pragma unroll
     for (int k = 0; k < EPT; ++k)
@@ -464,6 +467,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
           const int r = e / BS, c = e - BS * r;
           K[(int64_t)q * NE + e] = val[k];
           K[(int64_t)qt * NE + c * BS + r] = make_double2(val[k].x, -val[k].y);
+          if (g.kf32) {
+            float2* __restrict__ Kf = static_cast<float2*>(g.kf32);
+            Kf[(int64_t)q * SB + r * RS + c] = make_float2((float)val[k].x, (float)val[k].y);
+            Kf[(int64_t)qt * SB + c * RS + r] = make_float2((float)val[k].x, (float)-val[k].y);
+          }
         }
       }
     } else {
@@ -484,11 +492,57 @@ __global__ void __launch_bounds__(WARPS * 32, MINB_C) k_gemm13_c32(GemmArgs g) {
           const double2 tv = sK[c * BS + r];
           const double dr = val[k].x - tv.x, di = val[k].y + tv.y;
           herm = fmax(herm, sqrt(dr * dr + di * di));
-          K[(int64_t)q * NE + e] = make_double2(0.5 * (val[k].x + tv.x), 0.5 * (val[k].y - tv.y));
+          const double2 w = make_double2(0.5 * (val[k].x + tv.x), 0.5 * (val[k].y - tv.y));
+          K[(int64_t)q * NE + e] = w;
+          if (g.kf32)
+            static_cast<float2*>(g.kf32)[(int64_t)q * SB + r * RS + c] = make_float2((float)w.x, (float)w.y);
         }
       }
       for (int off = 16; off > 0; off >>= 1) herm = fmax(herm, __shfl_xor_sync(0xffffffffu, herm, off));
       if (lane == 0 && g.herm_max) amax_nonneg(g.herm_max, herm);
+    }
+  }
+  return WAIT_OK;
+}
+
+// One warp per item (output block); a persistent launch (g.persistent) walks
+// items with a grid-wide stride, and a grouped launch (g.grp) takes its items
+// from several products at once: item i is item gitems[i].y of the product
+// described by grp[gitems[i].x] (the same kernel and epilogue for all).
+template <int EPI, bool PK, int NS>
+__global__ void __launch_bounds__(WARPS * 32, minb_c(NS)) k_gemm13_c32(const __grid_constant__ GemmArgs g) {
+  constexpr int NT = 2;
+  constexpr int WBUF = NT * Slot<float2>::STRIDE;  // one stage of one warp (float2)
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int h = lane >> 4;
+  const int c = lane & 15;
+  int64_t item = (int64_t)blockIdx.x * WARPS + warp;
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  Smem* ctl = reinterpret_cast<Smem*>(dyn_smem);
+  float2* wsm = reinterpret_cast<float2*>(dyn_smem + 256) + (size_t)warp * NS * WBUF;
+  if (item >= g.n_items) return;  // whole warp leaves together
+  uint64_t* bar = ctl->bar[warp];
+  if (lane == 0) {
+    for (int st = 0; st < NS; ++st) mbar_init(&bar[st], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const int64_t stride = g.persistent ? (int64_t)gridDim.x * WARPS : g.n_items;
+  unsigned phase = 0u;
+  for (bool first = true; item < g.n_items; item += stride, first = false) {
+    if (!first) {
+      // the last epilogue wrote this warp's buffers through the generic proxy;
+      // order those writes before the next item's bulk copies land there
+      fence_proxy_async_smem();
+      __syncwarp();
+    }
+    const int2 gi = g.grp ? g.gitems[item] : make_int2(0, 0);
+    const int ok = c32_item<EPI, PK, NS>(g.grp ? g.grp[gi.x] : g, g.grp ? (int64_t)gi.y : item, wsm, bar, phase,
+                                         lane, h, c, g.wait_ns);
+    if (ok != WAIT_OK) {
+      if (lane == 0 && g.err) atomicMax(g.err, ok);
+      return;
     }
   }
 }
@@ -527,9 +581,10 @@ __global__ void __launch_bounds__(R_WARPS * 32, MINB_R) k_gemm13_r32(GemmArgs g)
 #pragma unroll
   for (int rr = 0; rr < RH; ++rr) acc[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
 
+  unsigned phase = 0u;
   const int ok = stream_triples<float, NT, R_STAGES>(
       wsm, bar, static_cast<const float*>(g.A), static_cast<const float*>(g.B), static_cast<const float*>(g.zero),
-      g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns, [&](const float* sA, const float* sB) {
+      g.ab, g.ptr[item], g.ptr[item + 1], lane, h, g.wait_ns, phase, [&](const float* sA, const float* sB) {
         float4 b[BS];  // B[m][4cl .. 4cl+3]
 #pragma unroll
         for (int m = 0; m < BS; ++m) b[m] = *reinterpret_cast<const float4*>(sB + m * RS + 4 * cl);
@@ -620,6 +675,33 @@ __global__ void __launch_bounds__(R_WARPS * 32, MINB_R) k_gemm13_r32(GemmArgs g)
   }
 }
 
+// One complex launch: NS stages per warp; a persistent launch runs at most
+// as many CTAs as are resident at once (SMs x CTAs per SM).
+template <int EPI, bool PK, int NS>
+void launch_c32(const GemmArgs& g, cudaStream_t st) {
+  constexpr size_t sm = smem_c(NS);
+  static bool attr_done = false;
+  if (!attr_done) {
+    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI, PK, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_done = true;
+  }
+  int64_t grid = (g.n_items + WARPS - 1) / WARPS;
+  if (g.persistent) {
+    int dev = 0, sms = 0;
+    RT_CUDA_CHECK(cudaGetDevice(&dev));
+    RT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid = std::min<int64_t>(grid, (int64_t)sms * minb_c(NS));
+  }
+  RT_REQUIRE(grid < (1ll << 31), RT_EINTERNAL, "grid too large");
+  k_gemm13_c32<EPI, PK, NS><<<(unsigned)grid, WARPS * 32, sm, st>>>(g);
+}
+
+template <int EPI, bool PK>
+void launch_c32_ns(const GemmArgs& g, cudaStream_t st) {
+  if (g.stages == 3) launch_c32<EPI, PK, 3>(g, st);
+  else launch_c32<EPI, PK, C_STAGES>(g, st);
+}
+
 }  // namespace f32
 
 // Launches the FP32 13-function kernels; false if the variant is not one of
@@ -628,34 +710,31 @@ bool launch_gemm13_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const Ge
   using namespace f32;
   RT_REQUIRE(!g.a_planar || (cplx && !a_dag && !b_dag), RT_EINTERNAL,
              "column-planar A only for complex products with untransposed operands");
+  RT_REQUIRE(g.stages == 0 || g.stages == C_STAGES || g.stages == 3, RT_EINTERNAL, "stages per warp: 2 or 3");
+  RT_REQUIRE(!(g.grp || g.persistent || g.stages) || cplx, RT_EINTERNAL,
+             "grouped, persistent and staged variants are complex-product launches");
   if (a_dag || b_dag) return false;
   if (g.n_items == 0) return true;
   RT_REQUIRE(g.zero != nullptr, RT_EINTERNAL, "FP32 products need a zero block");
-  const int64_t grid_c = (g.n_items + WARPS - 1) / WARPS;
   const int64_t grid_r = (g.n_items + R_WARPS - 1) / R_WARPS;
-  RT_REQUIRE(grid_c < (1ll << 31), RT_EINTERNAL, "grid too large");
-  const size_t smem_c = SMEM_C, smem_r = SMEM_R;
+  const size_t smem_r = SMEM_R;
   static bool attr_done = false;
   if (!attr_done) {
-    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_STORE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_DELTA_SANDWICH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_ADD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_STORE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-    RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_c32<EPI_DELTA_SANDWICH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_r32<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
     RT_CUDA_CHECK(cudaFuncSetAttribute(k_gemm13_r32<EPI_STORE_ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
     attr_done = true;
   }
   if (cplx && g.a_planar) {
-    if (epi == EPI_STORE) k_gemm13_c32<EPI_STORE, true><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
-    else if (epi == EPI_DELTA_SANDWICH) k_gemm13_c32<EPI_DELTA_SANDWICH, true><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+    if (epi == EPI_STORE) launch_c32_ns<EPI_STORE, true>(g, st);
+    else if (epi == EPI_DELTA_SANDWICH) launch_c32_ns<EPI_DELTA_SANDWICH, true>(g, st);
     else RT_REQUIRE(false, RT_EINTERNAL, "column-planar A only with the store and delta-sandwich epilogues");
   } else if (cplx) {
-    if (epi == EPI_STORE) k_gemm13_c32<EPI_STORE, false><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
-    else if (epi == EPI_ADD) k_gemm13_c32<EPI_ADD, false><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
-    else if (epi == EPI_DELTA_SANDWICH) k_gemm13_c32<EPI_DELTA_SANDWICH, false><<<(unsigned)grid_c, WARPS * 32, smem_c, st>>>(g);
+    if (epi == EPI_STORE) launch_c32_ns<EPI_STORE, false>(g, st);
+    else if (epi == EPI_ADD && !g.grp && !g.persistent && !g.stages) launch_c32<EPI_ADD, false, C_STAGES>(g, st);
+    else if (epi == EPI_DELTA_SANDWICH) launch_c32_ns<EPI_DELTA_SANDWICH, false>(g, st);
     else return false;
   } else {
+    RT_REQUIRE(grid_r < (1ll << 31), RT_EINTERNAL, "grid too large");
     if (epi == EPI_STORE) k_gemm13_r32<EPI_STORE><<<(unsigned)grid_r, R_WARPS * 32, smem_r, st>>>(g);
     else if (epi == EPI_STORE_ACC) k_gemm13_r32<EPI_STORE_ACC><<<(unsigned)grid_r, R_WARPS * 32, smem_r, st>>>(g);
     else return false;

@@ -12,6 +12,8 @@
 //   * epilogues are fused per lane: Taylor accumulation into U, store, add,
 //     and the delta-form sandwich K' = K + M + W dU^dagger with the mirror
 //     and the hermitian diagonal block.
+#include <algorithm>
+
 #include "rt_internal.cuh"
 
 namespace rt {
@@ -70,9 +72,7 @@ template <>
 __device__ __forceinline__ float2 zero_v<float2>() { return make_float2(0.f, 0.f); }
 
 template <typename V, bool BDAG, int EPI>
-__global__ void __launch_bounds__(THREADS, 2) k_gemm4_f32(GemmArgs g) {
-  const int64_t item = (int64_t)blockIdx.x * THREADS + threadIdx.x;
-  if (item >= g.n_items) return;
+__device__ __forceinline__ void g4_item(const GemmArgs& g, int64_t item) {
   const V* __restrict__ A = static_cast<const V*>(g.A);
   const V* __restrict__ B = static_cast<const V*>(g.B);
   V acc[NE];
@@ -97,6 +97,21 @@ __global__ void __launch_bounds__(THREADS, 2) k_gemm4_f32(GemmArgs g) {
   const int q = g.item_blk[item];
   if constexpr (EPI == EPI_STORE) {
     store_block(static_cast<V*>(g.C) + (int64_t)q * NE, acc);
+    if constexpr (sizeof(V) == 8) {
+      // delta form: also W = dK + M in FP32 (dK in FP64 through the map from
+      // this pattern to dK's; -1 = no dK block), one rounding per element
+      if (g.base) {
+        const int kq = g.add_map ? g.add_map[q] : q;
+        float2 w[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+          double2 kv = make_double2(0.0, 0.0);
+          if (kq >= 0) kv = static_cast<const double2*>(g.base)[(int64_t)kq * NE + e];
+          w[e] = make_float2((float)((double)acc[e].x + kv.x), (float)((double)acc[e].y + kv.y));
+        }
+        store_block(static_cast<float2*>(g.U) + (int64_t)q * NE, w);
+      }
+    }
   } else if constexpr (EPI == EPI_ADD) {
     V* C = static_cast<V*>(g.C) + (int64_t)q * NE;
     V old[NE];
@@ -140,17 +155,34 @@ __global__ void __launch_bounds__(THREADS, 2) k_gemm4_f32(GemmArgs g) {
       const int qt = g.tmap[q];
       // reference split: R = U K_ref U^dagger - K_ref (FP64) joins the base
       const double2* __restrict__ R = g.base2 ? static_cast<const double2*>(g.base2) + (int64_t)q * NE : nullptr;
+      // or R(E) = sum_p E^p B_p at this step's field, by Horner here
+      const double E = g.rpoly ? *g.poly_E : 0.0;
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int e = r * 4 + c;
           double2 kv = base[e];
-          if (R) kv = make_double2(kv.x + R[e].x, kv.y + R[e].y);
+          if (R) {
+            kv = make_double2(kv.x + R[e].x, kv.y + R[e].y);
+          } else if (g.rpoly) {
+            const int64_t idx = (int64_t)q * NE + e;
+            double2 rv = g.rpoly[g.rdeg][idx];
+            for (int p = g.rdeg - 1; p >= 0; --p) {
+              const double2 cp = g.rpoly[p][idx];
+              rv = make_double2(fma(rv.x, E, cp.x), fma(rv.y, E, cp.y));
+            }
+            kv = make_double2(kv.x + rv.x, kv.y + rv.y);
+          }
           const double2 v =
               make_double2(kv.x + ((double)mv[e].x + (double)acc[e].x), kv.y + ((double)mv[e].y + (double)acc[e].y));
           K[(int64_t)q * NE + e] = v;
           if (i != j) K[(int64_t)qt * NE + c * 4 + r] = make_double2(v.x, -v.y);
+          if (g.kf32 && i != j) {
+            float2* __restrict__ Kf = static_cast<float2*>(g.kf32);
+            Kf[(int64_t)q * NE + e] = make_float2((float)v.x, (float)v.y);
+            Kf[(int64_t)qt * NE + c * 4 + r] = make_float2((float)v.x, (float)-v.y);
+          }
         }
       if (i == j) {
         // diagonal block (one item in ~100): read the lane's own stores back,
@@ -166,7 +198,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_gemm4_f32(GemmArgs g) {
             const double2 a = v[r * 4 + c], t = v[c * 4 + r];
             const double dr = a.x - t.x, di = a.y + t.y;
             herm = fmax(herm, sqrt(dr * dr + di * di));
-            K[(int64_t)q * NE + r * 4 + c] = make_double2(0.5 * (a.x + t.x), 0.5 * (a.y - t.y));
+            const double2 w = make_double2(0.5 * (a.x + t.x), 0.5 * (a.y - t.y));
+            K[(int64_t)q * NE + r * 4 + c] = w;
+            if (g.kf32)
+              static_cast<float2*>(g.kf32)[(int64_t)q * NE + r * 4 + c] = make_float2((float)w.x, (float)w.y);
           }
         if (g.herm_max) atomicMax(g.herm_max, (unsigned long long)__double_as_longlong(herm));
       }
@@ -174,9 +209,28 @@ __global__ void __launch_bounds__(THREADS, 2) k_gemm4_f32(GemmArgs g) {
   }
 }
 
+// One lane per item (output block); a persistent launch (g.persistent) walks
+// items with a grid-wide stride, and a grouped launch (g.grp) takes item i as
+// item gitems[i].y of the product described by grp[gitems[i].x].
+template <typename V, bool BDAG, int EPI>
+__global__ void __launch_bounds__(THREADS, 2) k_gemm4_f32(const __grid_constant__ GemmArgs g) {
+  int64_t item = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+  const int64_t stride = g.persistent ? (int64_t)gridDim.x * THREADS : g.n_items;
+  for (; item < g.n_items; item += stride) {
+    const int2 gi = g.grp ? g.gitems[item] : make_int2(0, 0);
+    g4_item<V, BDAG, EPI>(g.grp ? g.grp[gi.x] : g, g.grp ? (int64_t)gi.y : item);
+  }
+}
+
 template <typename V, bool BDAG, int EPI>
 void launch_one(const GemmArgs& g, cudaStream_t st) {
-  const int64_t grid = (g.n_items + THREADS - 1) / THREADS;
+  int64_t grid = (g.n_items + THREADS - 1) / THREADS;
+  if (g.persistent) {
+    int dev = 0, sms = 0;
+    RT_CUDA_CHECK(cudaGetDevice(&dev));
+    RT_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid = std::min<int64_t>(grid, (int64_t)sms * 2);  // 2 CTAs per SM (launch bounds)
+  }
   RT_REQUIRE(grid < (1ll << 31), RT_EINTERNAL, "grid too large");
   k_gemm4_f32<V, BDAG, EPI><<<(unsigned)grid, THREADS, 0, st>>>(g);
   RT_CUDA_CHECK(cudaGetLastError());
@@ -188,6 +242,9 @@ void launch_one(const GemmArgs& g, cudaStream_t st) {
 // not one of theirs (the generic kernel then runs it).
 bool launch_gemm4_f32(bool cplx, bool a_dag, bool b_dag, Epilogue epi, const GemmArgs& g, cudaStream_t st) {
   using namespace f32b4;
+  RT_REQUIRE(!(g.grp || g.persistent) || cplx, RT_EINTERNAL, "grouped and persistent launches are complex products");
+  RT_REQUIRE(!g.base || (cplx && !b_dag && epi == EPI_STORE) || epi == EPI_DELTA_SANDWICH, RT_EINTERNAL,
+             "W = dK + M comes with the complex store epilogue");
   if (a_dag) return false;
   if (g.n_items == 0) return true;
   if (!cplx) {
