@@ -175,7 +175,8 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu capture of
 # the same kernel and workload, keyed by (path, kernel class); None when the kernel
 # changed after the capture.
-TRAFFIC = {}
+TRAFFIC = {("diamond 4096 atoms x 13 functions, r_S=r_H=7A, r_Sinv=r_T=r_U=r_K=r_M=10A, dt=0.05, EM 6 terms, "
+            "x-kick 1e-3", "fp32", "gemm_M=UK"): 24.574e9 + 2.604e9}  # k_gemm13_c32<EPI_STORE, packed>
 
 
 def derived_alu_peaks(torch, sm_max_mhz):

@@ -438,20 +438,34 @@ __device__ __forceinline__ int c32_item(const GemmArgs& g, int64_t item, float2*
         }
       }
     } else if (g.rpoly) {
-      // the same R at this step's field, R(E) = sum_p E^p B_p, by Horner here
+      // the same R at this step's field, R(E) = sum_p E^p B_p, by Horner here;
+      // coefficient by coefficient, so that the lane's loads of one B_p are
+      // in flight together
       const double E = *g.poly_E;
+      constexpr int HALF = (EPT + 1) / 2;  // elements per pass (register budget)
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const int e = lane + 32 * k;
-        if (e < NE) {
-          const int64_t idx = (int64_t)q * NE + e;
-          double2 rv = g.rpoly[g.rdeg][idx];
-          for (int p = g.rdeg - 1; p >= 0; --p) {
-            const double2 cp = g.rpoly[p][idx];
-            rv = make_double2(fma(rv.x, E, cp.x), fma(rv.y, E, cp.y));
-          }
-          val[k] = make_double2(val[k].x + rv.x, val[k].y + rv.y);
+      for (int k0 = 0; k0 < EPT; k0 += HALF) {
+        double2 rv[HALF];
+        const double2* __restrict__ top = g.rpoly[g.rdeg];
+#pragma unroll
+        for (int k = 0; k < HALF; ++k) {
+          const int e = lane + 32 * (k0 + k);
+          rv[k] = (k0 + k < EPT && e < NE) ? top[(int64_t)q * NE + e] : make_double2(0.0, 0.0);
         }
+        for (int p = g.rdeg - 1; p >= 0; --p) {
+          const double2* __restrict__ cp = g.rpoly[p];
+#pragma unroll
+          for (int k = 0; k < HALF; ++k) {
+            const int e = lane + 32 * (k0 + k);
+            if (k0 + k < EPT && e < NE) {
+              const double2 cv = cp[(int64_t)q * NE + e];
+              rv[k] = make_double2(fma(rv[k].x, E, cv.x), fma(rv[k].y, E, cv.y));
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < HALF; ++k)
+          if (k0 + k < EPT) val[k0 + k] = make_double2(val[k0 + k].x + rv[k].x, val[k0 + k].y + rv[k].y);
       }
     }
 #pragma unroll

@@ -58,9 +58,17 @@ def test_nan_in_h_is_reported(rt, system):
         ctx.close()
 
 
-def test_wait_timeout_then_resume_from_checkpoint(rt, system):
+@pytest.mark.parametrize("incremental", [0, 1])
+def test_wait_timeout_then_resume_from_checkpoint(rt, system, incremental):
+    """A bounded wait that gives up poisons the context; a restore that is
+    rejected (a truncated checkpoint) leaves it poisoned; a valid restore
+    resumes it.  The literal path resumes bit for bit; the reference split
+    forms dK = K - K_ref again from the restored K (one FP64 rounding)."""
     s, K0 = system
-    ref = rt.RT(s, precision="fp32", **_radii())
+    kw = dict(precision="fp32", **_radii())
+    if incremental:
+        kw.update(incremental=1, field_poly=1)
+    ref = rt.RT(s, **kw)
     ref.inverse()
     ref.set_density_dense(0, 0, K0)
     ref.kick(0, 0, 0, 1e-3)
@@ -69,7 +77,7 @@ def test_wait_timeout_then_resume_from_checkpoint(rt, system):
     K_ref = ref.matrix(0, rt.RT_MAT_K)
     ref.close()
 
-    ctx = rt.RT(s, precision="fp32", **_radii())
+    ctx = rt.RT(s, **kw)
     ctx.inverse()
     ctx.set_density_dense(0, 0, K0)
     ctx.kick(0, 0, 0, 1e-3)
@@ -82,13 +90,23 @@ def test_wait_timeout_then_resume_from_checkpoint(rt, system):
     with pytest.raises(rt.RTError) as e:  # poisoned until a checkpoint is restored
         ctx.step(1)
     assert e.value.status == rt.RT_ESTATE
+    with pytest.raises(rt.RTError) as e:  # a rejected restore clears nothing
+        ctx.set_state(state[:-8])
+    assert e.value.status == rt.RT_EINVAL
+    with pytest.raises(rt.RTError) as e:
+        ctx.step(1)
+    assert e.value.status == rt.RT_ESTATE
     ctx.set_state(state)
     ctx.step(2)
     obs = ctx.observables(0, 0)
     K = ctx.matrix(0, rt.RT_MAT_K)
     ctx.close()
-    assert np.array_equal(K, K_ref)
-    assert np.array_equal(obs[-2:], ref_obs[-2:])
+    if incremental:
+        assert np.abs(K - K_ref).max() <= 1e-12 * np.abs(K_ref).max()
+        assert np.abs(obs[-2:, 3] - ref_obs[-2:, 3]).max() <= 1e-12 * np.abs(ref_obs[-2:, 3]).max()
+    else:
+        assert np.array_equal(K, K_ref)
+        assert np.array_equal(obs[-2:], ref_obs[-2:])
 
 
 def test_unknown_fault_flag_rejected(rt, system):
