@@ -295,17 +295,21 @@ void launch_sum(const double* v, int64_t n, double* part, double sqrt_div, doubl
 // through kx_map (block (j,i) of X, or -1).  One warp per block (coalesced
 // reads of K), fixed block-to-warp assignment and fixed-order reductions: the
 // result does not depend on scheduling.
-__global__ void k_traces(const double2* __restrict__ K, int64_t nnzb, const int32_t* __restrict__ rowidx,
-                         const int32_t* __restrict__ col, const int32_t* __restrict__ bsize, int B,
-                         const double* __restrict__ S, const int32_t* __restrict__ ks_map,
-                         const double* __restrict__ Dx, const double* __restrict__ Dy, const double* __restrict__ Dz,
-                         const int32_t* __restrict__ kd_map, double* __restrict__ part) {
+// One CTA's share (block index blk of nblk) of the trace sums of one K; its
+// 8 partials go to part[blk * 8 ..].
+__device__ __forceinline__ void traces_cta(const double2* __restrict__ K, int64_t nnzb,
+                                           const int32_t* __restrict__ rowidx, const int32_t* __restrict__ col,
+                                           const int32_t* __restrict__ bsize, int B, const double* __restrict__ S,
+                                           const int32_t* __restrict__ ks_map, const double* __restrict__ Dx,
+                                           const double* __restrict__ Dy, const double* __restrict__ Dz,
+                                           const int32_t* __restrict__ kd_map, double* __restrict__ part, int blk,
+                                           int nblk) {
   __shared__ double s[4][RED_T / 32];
   double acc[4] = {0, 0, 0, 0};
   const int NE = B * B;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * (RED_T / 32) + warp;
-  const int64_t nw = (int64_t)gridDim.x * (RED_T / 32);
+  const int64_t gw = (int64_t)blk * (RED_T / 32) + warp;
+  const int64_t nw = (int64_t)nblk * (RED_T / 32);
   for (int64_t q = gw; q < nnzb; q += nw) {
     int i = rowidx[q], j = col[q];
     if (j < i) continue;
@@ -334,15 +338,32 @@ __global__ void k_traces(const double2* __restrict__ K, int64_t nnzb, const int3
     for (int c = 0; c < 4; ++c) {
       double t = 0.0;
       for (int w = 0; w < RED_T / 32; ++w) t += s[c][w];
-      part[blockIdx.x * 8 + 2 * c] = t;
-      part[blockIdx.x * 8 + 2 * c + 1] = 0.0;  // Im Tr(K X) = 0 for hermitian K, symmetric X
+      part[blk * 8 + 2 * c] = t;
+      part[blk * 8 + 2 * c + 1] = 0.0;  // Im Tr(K X) = 0 for hermitian K, symmetric X
     }
 }
 
+__global__ void k_traces(const double2* __restrict__ K, int64_t nnzb, const int32_t* __restrict__ rowidx,
+                         const int32_t* __restrict__ col, const int32_t* __restrict__ bsize, int B,
+                         const double* __restrict__ S, const int32_t* __restrict__ ks_map,
+                         const double* __restrict__ Dx, const double* __restrict__ Dy, const double* __restrict__ Dz,
+                         const int32_t* __restrict__ kd_map, double* __restrict__ part) {
+  traces_cta(K, nnzb, rowidx, col, bsize, B, S, ks_map, Dx, Dy, Dz, kd_map, part, blockIdx.x, gridDim.x);
+}
+
+// The same for every (system, kick) pair of a table: pair blockIdx.y, its
+// partials at part[pair * gridDim.x * 8 ..].
+__global__ void k_traces_grouped(const TracePair* __restrict__ tab, double* __restrict__ part) {
+  const TracePair& t = tab[blockIdx.y];
+  traces_cta(t.K, t.nnzb, t.rowidx, t.col, t.bsize, t.B, t.S, t.ks_map, t.Dx, t.Dy, t.Dz, t.kd_map,
+             part + (int64_t)blockIdx.y * gridDim.x * 8, blockIdx.x, gridDim.x);
+}
+
 // Sums the trace partials in fixed order and writes one observables record.
-__global__ void k_traces_final(const double* __restrict__ part, int nb, const DevState* st, int herm_slot,
-                               double* __restrict__ ring, int capacity, int n_slots, int slot_index,
-                               const double* __restrict__ ref, double* __restrict__ out) {
+__device__ __forceinline__ void traces_final_cta(const double* __restrict__ part, int nb, const DevState* st,
+                                                 int herm_slot, double* __restrict__ ring, int capacity, int n_slots,
+                                                 int slot_index, const double* __restrict__ ref,
+                                                 double* __restrict__ out) {
   __shared__ double s[8][RED_T];
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < nb; i += RED_T)
@@ -380,6 +401,20 @@ __global__ void k_traces_final(const double* __restrict__ part, int nb, const De
   }
 }
 
+__global__ void k_traces_final(const double* __restrict__ part, int nb, const DevState* st, int herm_slot,
+                               double* __restrict__ ring, int capacity, int n_slots, int slot_index,
+                               const double* __restrict__ ref, double* __restrict__ out) {
+  traces_final_cta(part, nb, st, herm_slot, ring, capacity, n_slots, slot_index, ref, out);
+}
+
+// One record per pair of the table (pair blockIdx.x)
+__global__ void k_traces_final_grouped(const TracePair* __restrict__ tab, const double* __restrict__ part, int nb,
+                                       const DevState* st, double* __restrict__ ring, int capacity, int n_slots) {
+  const TracePair& t = tab[blockIdx.x];
+  traces_final_cta(part + (int64_t)blockIdx.x * nb * 8, nb, st, t.herm_slot, ring, capacity, n_slots, t.slot_index,
+                   t.ref, nullptr);
+}
+
 void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const int32_t* col, const int32_t* bsize,
                    int B, const double* S, const int32_t* ks_map, const double* Dx, const double* Dy,
                    const double* Dz, const int32_t* kd_map, double* part, const DevState* st, int herm_slot,
@@ -388,6 +423,15 @@ void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const 
   int nb = reduce_blocks(nnzb);
   k_traces<<<nb, RED_T, 0, s>>>(K, nnzb, rowidx, col, bsize, B, S, ks_map, Dx, Dy, Dz, kd_map, part);
   k_traces_final<<<1, RED_T, 0, s>>>(part, nb, st, herm_slot, ring, capacity, n_slots, slot_index, ref, out);
+  RT_CUDA_CHECK(cudaGetLastError());
+}
+
+void launch_traces_grouped(const TracePair* tab, int n_pairs, int nb, double* part, const DevState* st, double* ring,
+                           int capacity, int n_slots, cudaStream_t s) {
+  if (n_pairs == 0) return;
+  RT_REQUIRE(nb >= 1 && nb <= RED_MAXB && n_pairs < 65536, RT_EINTERNAL, "grouped traces: bad launch shape");
+  k_traces_grouped<<<dim3((unsigned)nb, (unsigned)n_pairs), RED_T, 0, s>>>(tab, part);
+  k_traces_final_grouped<<<(unsigned)n_pairs, RED_T, 0, s>>>(tab, part, nb, st, ring, capacity, n_slots);
   RT_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -190,6 +190,11 @@ struct rt_ctx {
   rt::LaunchShape shape[rt::RT_N_STAGES];
   rt::StageGroup groups[rt::RT_N_STAGES];
   bool groups_built = false;
+  // grouped traces of every (system, kick) pair (reference split, several pairs)
+  rt::TracePair* d_tpairs = nullptr;
+  double* tpart = nullptr;
+  int n_tpairs = 0, tnb = 0;
+  double tbytes = 0.0;
   bool poisoned = false;
   bool unrecoverable = false;  // a drain of copies in flight gave up: shared memory may have been written late
   std::string err;
@@ -1412,6 +1417,45 @@ static void build_groups(rt_ctx* c) {
     G.planar = tab[0].a_planar;
     G.bdag = kstage && B == 4;  // the 4-function kernel transposes dU while loading
   }
+  // the traces of every pair in two launches, when there are several pairs
+  const int n_pairs = (int)c->sys.size() * c->p.n_kick;
+  if (n_pairs > 1) {
+    std::vector<TracePair> tp;
+    int64_t max_nnzb = 0;
+    int slot = 0;
+    for (auto& sp : c->sys) {
+      Sys& s = *sp;
+      for (int k = 0; k < c->p.n_kick; ++k, ++slot) {
+        TracePair t;
+        memset(&t, 0, sizeof(t));
+        t.K = s.dK[k];
+        t.nnzb = s.pK->nnzb;
+        t.rowidx = s.pK->rowidx;
+        t.col = s.pK->col;
+        t.bsize = s.d_bsize;
+        t.B = s.B;
+        t.S = s.S;
+        t.ks_map = s.k_to_sT;
+        t.Dx = s.D[0];
+        t.Dy = s.D[1];
+        t.Dz = s.D[2];
+        t.kd_map = s.k_to_hT;
+        t.herm_slot = slot;
+        t.slot_index = slot;
+        t.ref = s.tref;
+        tp.push_back(t);
+        max_nnzb = std::max<int64_t>(max_nnzb, s.pK->nnzb);
+        c->tbytes += 16.0 * nvals(s, s.pK) + 8.0 * 4 * nvals(s, s.pH);
+      }
+    }
+    c->tnb = reduce_blocks(max_nnzb);
+    c->d_tpairs = c->arena.get_n<TracePair>(tp.size());
+    c->tpart = c->arena.get_n<double>((size_t)tp.size() * c->tnb * 8);
+    RT_CUDA_CHECK(
+        cudaMemcpyAsync(c->d_tpairs, tp.data(), sizeof(TracePair) * tp.size(), cudaMemcpyHostToDevice, c->ws));
+    RT_CUDA_CHECK(cudaStreamSynchronize(c->ws));
+    c->n_tpairs = (int)tp.size();
+  }
   c->groups_built = true;
 }
 
@@ -1552,6 +1596,16 @@ static void enqueue_step(rt_ctx* c) {
   if (grouped)
     for (int st : {0, 2, 1, 3}) grouped_stage(c, st);  // every M product, then every K' product
   run(c, PC_MISC, 0, 0, [&] { launch_end_step(c->dstate, c->p.dt, c->ws); });
+  if (grouped && c->n_tpairs > 1) {
+    run(
+        c, PC_OBS, 0, c->tbytes,
+        [&] {
+          launch_traces_grouped(c->d_tpairs, c->n_tpairs, c->tnb, c->tpart, c->dstate, c->ring, c->p.obs_capacity,
+                                c->n_slots, c->ws);
+        },
+        2);
+    return;
+  }
   slot = 0;
   for (auto& sp : c->sys) {
     for (int k = 0; k < c->p.n_kick; ++k) observe(c, *sp, k, slot + k);

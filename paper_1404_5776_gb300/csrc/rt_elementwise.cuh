@@ -49,6 +49,23 @@ void launch_traces(const double2* K, int64_t nnzb, const int32_t* rowidx, const 
                    const double* Dz, const int32_t* kd_map, double* part, const DevState* st, int herm_slot,
                    double* ring, int capacity, int n_slots, int slot_index, cudaStream_t s,
                    const double* ref = nullptr, double* out = nullptr);
+// Arguments of the traces of one (system, kick) pair (as launch_traces takes them)
+struct TracePair {
+  const double2* K;
+  int64_t nnzb;
+  const int32_t *rowidx, *col, *bsize;
+  int B;
+  const double* S;
+  const int32_t* ks_map;
+  const double *Dx, *Dy, *Dz;
+  const int32_t* kd_map;
+  int herm_slot, slot_index;
+  const double* ref;
+};
+// launch_traces for every pair of a device table in two launches: nb CTAs per pair (reduce_blocks of the
+// largest pair), partials in part[n_pairs][nb][8], one observables record per pair
+void launch_traces_grouped(const TracePair* tab, int n_pairs, int nb, double* part, const DevState* st, double* ring,
+                           int capacity, int n_slots, cudaStream_t s);
 // dU = U - I stochastically rounded to FP32 (draws keyed on s->step and the element) and its per-block
 // conjugate transpose dUH (if non-null), from an FP64 U; with `planar` (13-function blocks) dU is written
 // column-planar (per column: real parts of rows 0..15, then imaginary parts), dUH in the row layout
