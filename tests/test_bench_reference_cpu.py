@@ -24,3 +24,18 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_roofline_traffic_is_keyed_to_the_default_workload(monkeypatch):
+    """The DRAM traffic of the dominant kernel that the benchmark line reports
+    is keyed to the workload name the default run produces: a renamed
+    workload would silently report null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    args = bench.parse()
+    key = (bench.cfg_name(args), "fp32", "gemm_M=UK")
+    assert key in bench.TRAFFIC and bench.TRAFFIC[key] > 0
+    # a different workload has no capture
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--radius", "8"])
+    assert (bench.cfg_name(bench.parse()), "fp32", "gemm_M=UK") not in bench.TRAFFIC
